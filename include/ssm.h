@@ -1,0 +1,179 @@
+/*
+ * ssm.h -- C ABI of the GB300 LADMM solver for spatial-spectral compartment mapping.
+ *
+ * The library estimates nonnegative compartment maps F (Q x N) from multi-contrast
+ * data M (P x N) and a dictionary K (P x Q) by solving
+ *
+ *     min_{F >= 0}  1/2 ||M - K F||_F^2 + lambda * 1/2 ||D F||^2            (Eq. 7, Eq. 8)
+ *
+ * with the linearized ADMM iteration of Algorithm 2 (Sec. III-F). D is the spatial
+ * finite-difference operator of Eq. 8 on an axis-aligned 1D/2D/3D voxel grid with a
+ * free (maskless) boundary: 2 neighbours per axis, fewer at the image edge.
+ *
+ * Two forms of the per-voxel f-step are offered:
+ *   SSM_FORM_LOWRANK  the rank-r form of Eq. 27/28, exactly as Algorithm 2 (the paper's
+ *                     proposed method); HBM-bandwidth bound.
+ *   SSM_FORM_DENSE    the full-rank form of Eq. 26, f_n = (K^T K + beta I)^{-1} c_n, a
+ *                     Q x Q by Q x N contraction every iteration (FP32 SIMT, or BF16 split
+ *                     hi+lo products on the tcgen05 tensor cores with FP32 accumulation).
+ *
+ * Conventions for every entry point:
+ *   - Layouts are row-major. K is P x Q (row p = one contrast encoding). M is P x N and
+ *     F is Q x N, "map-major": row p (or q) is one image over the N voxels, with the
+ *     voxel index n = x + nx*(y + ny*z) (x fastest). Leading dimensions are in elements.
+ *   - Device pointers must be CUDA device memory on the plan's device; host pointers
+ *     are ordinary host memory (pinned memory makes the copies asynchronous).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     All GPU work is enqueued on it; calls that return host values synchronise it.
+ *   - Errors are reported only by the returned status (never by a device trap);
+ *     ssm_last_error() gives a human-readable message for the calling thread.
+ *   - Ownership: the caller owns K, M, F and `info`; the plan owns every device buffer
+ *     it allocates (factors, state, workspace) and ssm_destroy releases them.
+ */
+#ifndef SSM_H
+#define SSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssm_plan_s* ssm_plan_t;
+
+typedef enum {
+  SSM_OK = 0,
+  SSM_EINVAL = 1,          /* invalid argument (sizes, pointers, parameters)        */
+  SSM_ENOMEM = 2,          /* device allocation failed                              */
+  SSM_ECUDA = 3,           /* a CUDA runtime/driver call failed                     */
+  SSM_ENAN = 4,            /* a residual became NaN or Inf                          */
+  SSM_ETIMEOUT = 5,        /* a bounded device-side wait gave up                    */
+  SSM_EUNSUPPORTED = 6,    /* valid request outside what this build implements      */
+  SSM_ENOTCONVERGED = 7    /* tolerance set but not reached within max_iter (info)  */
+} ssm_status;
+
+typedef enum {
+  SSM_FORM_LOWRANK = 0,    /* Algorithm 2 with the rank-r f-step of Eq. 28          */
+  SSM_FORM_DENSE = 1       /* full-rank f-step of Eq. 26                            */
+} ssm_form;
+
+typedef enum {
+  SSM_FP32 = 0,            /* FP32 arithmetic, FP32 state                           */
+  SSM_BF16X3 = 1           /* dense form: BF16 hi/lo split products (3 tcgen05 MMAs
+                              per tile, FP32 accumulation), FP32 state              */
+} ssm_precision;
+
+typedef struct {
+  int ndim;                /* 1, 2 or 3                                             */
+  int64_t dims[3];         /* grid (nx, ny, nz); unused trailing dims ignored       */
+  int P, Q;                /* dictionary size                                       */
+  double lambda;           /* regularisation weight of Eq. 7, >= 0                  */
+  double beta;             /* ADMM penalty, > 0 (the paper tunes it, Sec. III-E)    */
+  double xi_p;             /* z-step proximal weight; <= 0 selects Eq. 32:
+                              0.75 * lambda * ||D^T D|| + 1e-10                     */
+  int form;                /* ssm_form                                              */
+  int rank;                /* low-rank form: 0 = smallest r with
+                              ||K - K_r||_F < rank_tol ||K||_F (Sec. III-E), > 0 = r */
+  double rank_tol;         /* <= 0 selects 5e-5 (the paper's 0.005 %)               */
+  int precision;           /* ssm_precision (dense form; low-rank runs FP32)        */
+  int stencil_pairs;       /* 2 = literal Eq. 8 (each neighbour pair counted from
+                              both ends, D^T D = 2 L); 1 = once per pair (D^T D = L) */
+  int max_iter;            /* iteration budget (>= 0)                               */
+  int check_every;         /* residual test period; 0 = never test                  */
+  double tol_primal;       /* stop when ||z-f|| <= tol_primal ||z|| ...            */
+  double tol_change;       /* ... and ||z^{k+1}-z^k|| <= tol_change ||z^{k+1}||;
+                              a tolerance <= 0 is not used; none used = fixed budget */
+} ssm_params;
+
+typedef struct {
+  int status;              /* ssm_status of the solve                               */
+  int iterations;          /* iterations run                                        */
+  int rank;                /* r used by the low-rank form (min(P,Q) for dense)      */
+  int gram_side;           /* 0: eigenpairs from K K^T (P x P); 1: from K^T K       */
+  double xi_p;             /* xi_p used                                             */
+  double dtd_norm;         /* ||D^T D|| (closed form for the box grid)              */
+  double sigma1;           /* largest singular value of K                           */
+  double res_primal;       /* ||z - f|| / ||z|| at the last test (-1: none)          */
+  double res_change;       /* ||z^{k+1} - z^k|| / ||z^{k+1}|| at the last test      */
+  double plan_ms;          /* device time of ssm_plan                               */
+} ssm_info;
+
+/* Fill `p` with defaults: 2D, lambda 0, beta 1, xi_p rule, low-rank auto rank,
+ * literal stencil, FP32, max_iter 300, check_every 10, no tolerance. */
+ssm_status ssm_default_params(ssm_params* p);
+
+/*
+ * Plan a solver for one dictionary and one grid (Algorithm 2, steps 1-3).
+ *   K_host : P x Q row-major doubles on the host, read during the call only.
+ * Work done (on `stream`, device `device`): K is copied to the device; the Gram
+ * matrix of the smaller side (K K^T if P <= Q, else K^T K) is formed in FP64 and
+ * eigendecomposed by cyclic Jacobi in FP64, giving sigma_i, u_i, v_i of Eq. 27; the
+ * rank rule of Sec. III-E picks r; the weights sigma_i^2 / (beta^2 + beta sigma_i^2)
+ * of Eq. 28 (low-rank) or the matrix (K^T K + beta I)^{-1} of Eq. 26 (dense) are
+ * formed in FP64; xi_p follows Eq. 32 unless given. The per-voxel state (z, d and
+ * per-voxel projections) is allocated for N = prod(dims) voxels.
+ * Returns SSM_EINVAL for bad sizes/parameters, SSM_ENOMEM if the state does not fit.
+ * On success *out owns every allocation; on failure *out is NULL.
+ */
+ssm_status ssm_plan(ssm_plan_t* out, const ssm_params* p, const double* K_host,
+                    int device, void* stream);
+
+/*
+ * Run the LADMM iteration (Algorithm 2, steps 4-12) on data M and write F = z.
+ *   M_dev : P x N floats on the device, leading dimension ldm >= N; read only.
+ *   F_dev : Q x N floats on the device, leading dimension ldf >= N; written.
+ *   info  : host struct, may be NULL; filled after the solve (synchronises `stream`).
+ * z, f and d start at 0 (Algorithm 2, step 2). The projections of M on the singular
+ * vectors (g_n of step 4) are formed once with FP64 accumulation. The returned F is
+ * the feasible iterate z (F >= 0 elementwise). With a tolerance set, residuals are
+ * tested every check_every iterations (a host read of three FP64 sums); the status
+ * is SSM_ENOTCONVERGED when the budget ran out first (F is still written).
+ * Calls on one plan must not overlap (the plan holds the iteration state).
+ */
+ssm_status ssm_solve(ssm_plan_t plan, const float* M_dev, int64_t ldm, float* F_dev,
+                     int64_t ldf, ssm_info* info, void* stream);
+
+/*
+ * Same as ssm_solve with HOST buffers: M_host (P x N, ldm) is copied in, the solve
+ * runs, F_host (Q x N, ldf) is copied out; returns after the copy-out completes.
+ * Staging buffers are the plan's own (allocated at plan time).
+ */
+ssm_status ssm_solve_host(ssm_plan_t plan, const float* M_host, int64_t ldm,
+                          float* F_host, int64_t ldf, ssm_info* info, void* stream);
+
+/*
+ * Objective of Eq. 7 / Eq. 8 for given F (device, Q x N, ldf) and M (device, P x N):
+ *   1/2 ||M - K' F||_F^2 + lambda * 1/2 ||D F||^2,
+ * with K' the dictionary the plan iterates with (K for the dense form, the truncated
+ * K_r of Eq. 27 for the low-rank form) unless use_full_k != 0 (then K). The product
+ * K' F is FP32 with FP32 accumulation; both sums are accumulated in FP64.
+ * Writes *J_host and synchronises `stream`.
+ */
+ssm_status ssm_objective(ssm_plan_t plan, const float* M_dev, int64_t ldm,
+                         const float* F_dev, int64_t ldf, int use_full_k,
+                         double* J_host, void* stream);
+
+/*
+ * Read back the plan's factors (for tests): sigma (min(P,Q) doubles, descending) and,
+ * when non-NULL, V_r (Q x r row-major doubles, the first r right singular vectors).
+ */
+ssm_status ssm_plan_factors(ssm_plan_t plan, double* sigma_host, double* vr_host,
+                            int* rank_out);
+
+/* Free everything the plan owns. NULL is accepted. Synchronises the plan's device. */
+ssm_status ssm_destroy(ssm_plan_t plan);
+
+/* Static description of a status code. */
+const char* ssm_status_string(int status);
+
+/* Last error message recorded on the calling thread ("" if none). */
+const char* ssm_last_error(void);
+
+/* Number of kernel launches the library has issued on this process (all plans). */
+int64_t ssm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSM_H */
