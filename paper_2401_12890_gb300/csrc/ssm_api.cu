@@ -1,0 +1,569 @@
+// C ABI of the solver (include/ssm.h): parameter checks, the plan (Algorithm 2,
+// steps 1-3), the solve loop (steps 4-12 with the stopping rule) and the objective.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "ssm_internal.cuh"
+
+namespace ssm {
+
+std::atomic<int64_t> g_launches{0};
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+namespace {
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// ||D^T D|| for the free-boundary box grid: D^T D = s L and the grid Laplacian's
+// largest eigenvalue is sum over axes of 2 - 2 cos(pi (n_d - 1)/n_d) (path graphs).
+double dtd_norm_closed(const int64_t* dims, int ndim, int pairs) {
+  const double s = pairs == 2 ? 2.0 : 1.0;
+  double t = 0.0;
+  for (int d = 0; d < ndim; ++d)
+    if (dims[d] >= 2) t += 2.0 - 2.0 * std::cos(M_PI * (double)(dims[d] - 1) / (double)dims[d]);
+  return s * t;
+}
+
+int padded_rank(int r) {
+  static const int opts[] = {4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64};
+  for (int o : opts)
+    if (r <= o) return o;
+  return -1;
+}
+
+template <typename T>
+ssm_status dalloc(T** p, size_t count, cudaStream_t s) {
+  *p = nullptr;
+  if (count == 0) return SSM_OK;
+  SSM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(T) * count, s));
+  return SSM_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+ssm_status validate(const ssm_params* p) {
+  if (!p) {
+    set_error("params is NULL");
+    return SSM_EINVAL;
+  }
+  if (p->ndim < 1 || p->ndim > 3) {
+    set_error("ndim must be 1, 2 or 3");
+    return SSM_EINVAL;
+  }
+  int64_t N = 1;
+  for (int d = 0; d < p->ndim; ++d) {
+    if (p->dims[d] < 1 || p->dims[d] > (int64_t)1 << 31) {
+      set_error("grid dimensions must be >= 1");
+      return SSM_EINVAL;
+    }
+    N *= p->dims[d];
+  }
+  if (N > ((int64_t)1 << 34)) {
+    set_error("too many voxels");
+    return SSM_EINVAL;
+  }
+  if (p->P < 1 || p->Q < 1 || p->P > 65536 || p->Q > 65536) {
+    set_error("P and Q must be in [1, 65536]");
+    return SSM_EINVAL;
+  }
+  if (!(p->beta > 0.0) || !std::isfinite(p->beta)) {
+    set_error("beta must be > 0");
+    return SSM_EINVAL;
+  }
+  if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) {
+    set_error("lambda must be >= 0");
+    return SSM_EINVAL;
+  }
+  if (p->form != SSM_FORM_LOWRANK && p->form != SSM_FORM_DENSE) {
+    set_error("unknown form");
+    return SSM_EINVAL;
+  }
+  if (p->precision != SSM_FP32 && p->precision != SSM_BF16X3) {
+    set_error("unknown precision");
+    return SSM_EINVAL;
+  }
+  if (p->stencil_pairs != 1 && p->stencil_pairs != 2) {
+    set_error("stencil_pairs must be 1 or 2");
+    return SSM_EINVAL;
+  }
+  if (p->max_iter < 0 || p->check_every < 0 || p->rank < 0) {
+    set_error("max_iter, check_every and rank must be >= 0");
+    return SSM_EINVAL;
+  }
+  return SSM_OK;
+}
+
+void release(ssm_plan_s* pl) {
+  if (!pl) return;
+  tc_release(pl);
+  dfree(pl->K64);
+  dfree(pl->Bp64);
+  dfree(pl->Kt64);
+  dfree(pl->sig64);
+  dfree(pl->alpha64);
+  dfree(pl->K32);
+  dfree(pl->Kr32);
+  dfree(pl->V32);
+  dfree(pl->coefA);
+  dfree(pl->coefW);
+  dfree(pl->Mq32);
+  dfree(pl->Mhi);
+  dfree(pl->Mlo);
+  dfree(pl->Gq32);
+  for (int i = 0; i < 2; ++i) {
+    dfree(pl->Z[i]);
+    dfree(pl->Dl[i]);
+    dfree(pl->U[i]);
+    dfree(pl->Whi[i]);
+    dfree(pl->Wlo[i]);
+  }
+  dfree(pl->C32);
+  dfree(pl->S);
+  dfree(pl->H);
+  dfree(pl->Wf);
+  dfree(pl->Acc);
+  dfree(pl->Res);
+  dfree(pl->Mstage);
+  dfree(pl->Fstage);
+  dfree(pl->red);
+  dfree(pl->red_out);
+  if (pl->red_host) cudaFreeHost(pl->red_host);
+  if (pl->ev0) cudaEventDestroy(pl->ev0);
+  if (pl->ev1) cudaEventDestroy(pl->ev1);
+  delete pl;
+}
+
+ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
+  const ssm_params& p = pl->p;
+  SSM_CUDA(cudaEventCreate(&pl->ev0));
+  SSM_CUDA(cudaEventCreate(&pl->ev1));
+  SSM_CUDA(cudaEventRecord(pl->ev0, s));
+  const int P = p.P, Q = p.Q;
+  pl->P = P;
+  pl->Q = Q;
+  pl->g.nx = (int)p.dims[0];
+  pl->g.ny = p.ndim >= 2 ? (int)p.dims[1] : 1;
+  pl->g.nz = p.ndim >= 3 ? (int)p.dims[2] : 1;
+  pl->g.N = (int64_t)pl->g.nx * pl->g.ny * pl->g.nz;
+  pl->g.ld = round_up(pl->g.N, 128);
+  pl->dtd_norm = dtd_norm_closed(p.dims, p.ndim, p.stencil_pairs);
+  pl->xi = p.xi_p > 0.0 ? p.xi_p : 0.75 * p.lambda * pl->dtd_norm + 1e-10;  // Eq. 32
+  pl->lam_s = p.lambda * (p.stencil_pairs == 2 ? 2.0 : 1.0);
+  pl->n = std::min(P, Q);
+  pl->gram_side = P <= Q ? 0 : 1;
+  const int n = pl->n;
+
+  // dictionary and its Gram eigendecomposition (FP64)
+  SSM_TRY(dalloc(&pl->K64, (size_t)P * Q, s));
+  SSM_CUDA(cudaMemcpyAsync(pl->K64, K_host, sizeof(double) * P * Q, cudaMemcpyHostToDevice, s));
+  double *A = nullptr, *E = nullptr, *scratch = nullptr;
+  SSM_TRY(dalloc(&A, (size_t)n * n, s));
+  SSM_TRY(dalloc(&E, (size_t)n * n, s));
+  SSM_TRY(dalloc(&scratch, (size_t)n * n + 2, s));
+  SSM_TRY(gram_fp64(pl->K64, P, Q, pl->gram_side, A, s));
+  std::vector<double> evals;
+  ssm_status st = jacobi_eigen(A, n, E, scratch, evals, s);
+  if (st != SSM_OK) {
+    cudaFreeAsync(A, s);
+    cudaFreeAsync(E, s);
+    cudaFreeAsync(scratch, s);
+    return st;
+  }
+  pl->perm.resize(n);
+  std::iota(pl->perm.begin(), pl->perm.end(), 0);
+  std::stable_sort(pl->perm.begin(), pl->perm.end(),
+                   [&](int a, int b) { return evals[a] > evals[b]; });
+  pl->sigma.resize(n);
+  for (int i = 0; i < n; ++i) pl->sigma[i] = std::sqrt(std::max(0.0, evals[pl->perm[i]]));
+  pl->sigma1 = pl->sigma[0];
+
+  // rank (Sec. III-E): smallest r with ||K - K_r||_F < tol ||K||_F
+  if (p.form == SSM_FORM_LOWRANK) {
+    if (p.rank > 0) {
+      pl->r = std::min(p.rank, n);
+    } else {
+      const double tol = p.rank_tol > 0 ? p.rank_tol : 5e-5;
+      double total = 0.0;
+      for (double v : pl->sigma) total += v * v;
+      int r = n;
+      for (int c = 0; c <= n; ++c) {
+        double tail = 0.0;
+        for (int i = c; i < n; ++i) tail += pl->sigma[i] * pl->sigma[i];
+        if (total > 0 && std::sqrt(tail / total) < tol) {
+          r = c;
+          break;
+        }
+      }
+      pl->r = std::max(r, 1);
+    }
+    pl->R = padded_rank(pl->r);
+    if (pl->R < 0) {
+      cudaFreeAsync(A, s);
+      cudaFreeAsync(E, s);
+      cudaFreeAsync(scratch, s);
+      set_error("low-rank form supports r <= 64; use the dense form for higher ranks");
+      return SSM_EUNSUPPORTED;
+    }
+  } else {
+    pl->r = n;
+    pl->R = 0;
+  }
+  pl->Qp = (int)round_up(Q, 64);
+
+  SSM_TRY(dalloc(&pl->Bp64, (size_t)P * n, s));
+  SSM_TRY(dalloc(&pl->Kt64, (size_t)Q * n, s));
+  SSM_TRY(dalloc(&pl->sig64, (size_t)n, s));
+  SSM_TRY(dalloc(&pl->alpha64, (size_t)n, s));
+  SSM_TRY(dalloc(&pl->K32, (size_t)P * Q, s));
+  SSM_TRY(dalloc(&pl->Kr32, (size_t)P * Q, s));
+  if (p.form == SSM_FORM_LOWRANK) {
+    SSM_TRY(dalloc(&pl->V32, (size_t)Q * pl->R, s));
+    SSM_TRY(dalloc(&pl->coefA, (size_t)pl->R, s));
+    SSM_TRY(dalloc(&pl->coefW, (size_t)pl->R, s));
+  } else {
+    SSM_TRY(dalloc(&pl->Gq32, (size_t)Q * n, s));
+    SSM_TRY(dalloc(&pl->Mq32, (size_t)Q * pl->Qp, s));
+    if (p.precision == SSM_BF16X3) {
+      SSM_TRY(dalloc(&pl->Mhi, (size_t)Q * pl->Qp, s));
+      SSM_TRY(dalloc(&pl->Mlo, (size_t)Q * pl->Qp, s));
+    }
+  }
+  st = factors_fp64(pl, E, s);
+  cudaFreeAsync(A, s);
+  cudaFreeAsync(E, s);
+  cudaFreeAsync(scratch, s);
+  if (st != SSM_OK) return st;
+  if (p.form == SSM_FORM_DENSE) SSM_TRY(form_dense_inverse(pl, s));
+
+  // per-voxel state
+  const size_t QN = (size_t)Q * pl->g.ld;
+  for (int i = 0; i < 2; ++i) {
+    SSM_TRY(dalloc(&pl->Z[i], QN, s));
+    SSM_TRY(dalloc(&pl->Dl[i], QN, s));
+  }
+  int maxparts = 1;
+  if (p.form == SSM_FORM_LOWRANK) {
+    SSM_TRY(dalloc(&pl->S, (size_t)pl->R * pl->g.ld, s));
+    for (int i = 0; i < 2; ++i) SSM_TRY(dalloc(&pl->U[i], (size_t)pl->R * pl->g.ld, s));
+    maxparts = lowrank_max_partials(pl);
+  } else {
+    SSM_TRY(dalloc(&pl->C32, (size_t)n * pl->g.ld, s));
+    SSM_TRY(dalloc(&pl->H, QN, s));
+    if (p.precision == SSM_FP32) {
+      SSM_TRY(dalloc(&pl->Wf, QN, s));
+      SSM_TRY(dalloc(&pl->Acc, QN, s));
+      maxparts = dense_max_partials(pl);
+    } else {
+      for (int i = 0; i < 2; ++i) {
+        SSM_TRY(dalloc(&pl->Whi[i], QN, s));
+        SSM_TRY(dalloc(&pl->Wlo[i], QN, s));
+      }
+      SSM_TRY(tc_prepare(pl, s));
+      maxparts = std::max(tc_max_partials(pl), dense_max_partials(pl));
+    }
+  }
+  maxparts = std::max(maxparts, (int)((pl->g.N + 255) / 256));  // objective partials
+  pl->red_cap = maxparts;
+  SSM_TRY(dalloc(&pl->red, (size_t)maxparts * 4, s));
+  SSM_TRY(dalloc(&pl->red_out, 4, s));
+  SSM_CUDA(cudaMallocHost(&pl->red_host, 4 * sizeof(double)));
+  SSM_CUDA(cudaEventRecord(pl->ev1, s));
+  SSM_CUDA(cudaEventSynchronize(pl->ev1));
+  SSM_CUDA(cudaEventElapsedTime(&pl->plan_ms, pl->ev0, pl->ev1));
+  return SSM_OK;
+}
+
+// residual test: returns (rp, rc) from the three FP64 sums
+ssm_status read_residuals(ssm_plan_s* pl, int nparts, cudaStream_t s, double* rp, double* rc) {
+  SSM_TRY(finish_partials(pl->red, nparts, 3, pl->red_out, s));
+  SSM_CUDA(cudaMemcpyAsync(pl->red_host, pl->red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                           s));
+  SSM_CUDA(cudaStreamSynchronize(s));
+  const double zn = std::max(pl->red_host[2], 1e-300);
+  *rp = std::sqrt(pl->red_host[0] / zn);
+  *rc = std::sqrt(pl->red_host[1] / zn);
+  if (!std::isfinite(pl->red_host[0]) || !std::isfinite(pl->red_host[1]) ||
+      !std::isfinite(pl->red_host[2])) {
+    set_error("residual is not finite");
+    return SSM_ENAN;
+  }
+  return SSM_OK;
+}
+
+ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, int* nparts, cudaStream_t s) {
+  const ssm_params& p = pl->p;
+  if (p.form == SSM_FORM_LOWRANK) return lowrank_iteration(pl, cur, check, pl->red, nparts, s);
+  if (p.precision == SSM_FP32) {
+    // acc = M w (w^0 = 0, so the first product is 0)
+    SSM_TRY(sgemm(pl->Q, (int)pl->g.N, pl->Q, 1.f, pl->Mq32, pl->Qp, pl->Wf, pl->g.ld, 0.f,
+                  pl->Acc, pl->g.ld, s));
+    return dense_update(pl, cur, pl->Acc, check, true, false, pl->red, nparts, s);
+  }
+  return tc_iteration(pl, cur, check, pl->red, nparts, s);
+}
+
+ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int64_t ldf,
+                      ssm_info* info, cudaStream_t s) {
+  const ssm_params& p = pl->p;
+  const int64_t ld = pl->g.ld;
+  const size_t QN = (size_t)pl->Q * ld;
+  // step 4: projections of the data on the singular vectors (FP64 accumulation)
+  if (p.form == SSM_FORM_LOWRANK) {
+    SSM_TRY(project_data(pl, M, ldm, pl->r, s));
+    if (pl->R > pl->r)
+      SSM_CUDA(cudaMemsetAsync(pl->S + (size_t)pl->r * ld, 0,
+                               sizeof(float) * (size_t)(pl->R - pl->r) * ld, s));
+    SSM_CUDA(cudaMemsetAsync(pl->U[0], 0, sizeof(float) * (size_t)pl->R * ld, s));
+  } else {
+    SSM_TRY(project_data(pl, M, ldm, pl->n, s));
+    // h = M g = sum_i Gq_i c_i
+    SSM_TRY(sgemm(pl->Q, (int)pl->g.N, pl->n, 1.f, pl->Gq32, pl->n, pl->C32, ld, 0.f, pl->H, ld,
+                  s));
+    if (pl->Wf) SSM_CUDA(cudaMemsetAsync(pl->Wf, 0, sizeof(float) * QN, s));
+    if (pl->Whi[0]) {
+      SSM_CUDA(cudaMemsetAsync(pl->Whi[0], 0, sizeof(__nv_bfloat16) * QN, s));
+      SSM_CUDA(cudaMemsetAsync(pl->Wlo[0], 0, sizeof(__nv_bfloat16) * QN, s));
+    }
+  }
+  // step 2: z = d = 0
+  SSM_CUDA(cudaMemsetAsync(pl->Z[0], 0, sizeof(float) * QN, s));
+  SSM_CUDA(cudaMemsetAsync(pl->Dl[0], 0, sizeof(float) * QN, s));
+
+  const bool use_tol = p.tol_primal > 0 || p.tol_change > 0;
+  int cur = 0, k = 0;
+  double rp = -1, rc = -1;
+  ssm_status result = SSM_OK;
+  bool converged = false;
+  while (k < p.max_iter) {
+    const bool last = (k + 1 == p.max_iter);
+    const bool at_check = p.check_every > 0 && ((k + 1) % p.check_every == 0);
+    const bool check = (use_tol && at_check) || last;
+    int nparts = 0;
+    SSM_TRY(one_iteration(pl, cur, check, &nparts, s));
+    cur ^= 1;
+    ++k;
+    if (check) {
+      SSM_TRY(read_residuals(pl, nparts, s, &rp, &rc));
+      if (use_tol && at_check) {
+        const bool ok_p = p.tol_primal <= 0 || rp <= p.tol_primal;
+        const bool ok_c = p.tol_change <= 0 || rc <= p.tol_change;
+        if (ok_p && ok_c) {
+          converged = true;
+          break;
+        }
+      }
+    }
+  }
+  if (use_tol && !converged) result = SSM_ENOTCONVERGED;
+  // F = z (the feasible iterate)
+  SSM_CUDA(cudaMemcpy2DAsync(F, sizeof(float) * ldf, pl->Z[cur], sizeof(float) * ld,
+                             sizeof(float) * pl->g.N, pl->Q, cudaMemcpyDeviceToDevice, s));
+  if (info) {
+    SSM_CUDA(cudaStreamSynchronize(s));
+    info->status = result;
+    info->iterations = k;
+    info->rank = pl->r;
+    info->gram_side = pl->gram_side;
+    info->xi_p = pl->xi;
+    info->dtd_norm = pl->dtd_norm;
+    info->sigma1 = pl->sigma1;
+    info->res_primal = rp;
+    info->res_change = rc;
+    info->plan_ms = pl->plan_ms;
+  }
+  return result;
+}
+
+}  // namespace
+}  // namespace ssm
+
+using namespace ssm;
+
+extern "C" {
+
+ssm_status ssm_default_params(ssm_params* p) {
+  if (!p) return SSM_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->ndim = 2;
+  p->dims[0] = p->dims[1] = p->dims[2] = 1;
+  p->lambda = 0.0;
+  p->beta = 1.0;
+  p->xi_p = 0.0;
+  p->form = SSM_FORM_LOWRANK;
+  p->rank = 0;
+  p->rank_tol = 5e-5;
+  p->precision = SSM_FP32;
+  p->stencil_pairs = 2;
+  p->max_iter = 300;
+  p->check_every = 10;
+  return SSM_OK;
+}
+
+ssm_status ssm_plan(ssm_plan_t* out, const ssm_params* p, const double* K_host, int device,
+                    void* stream) {
+  if (!out) {
+    set_error("out is NULL");
+    return SSM_EINVAL;
+  }
+  *out = nullptr;
+  SSM_TRY(validate(p));
+  if (!K_host) {
+    set_error("K_host is NULL");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(device));
+  auto* pl = new ssm_plan_s();
+  pl->p = *p;
+  pl->device = device;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ssm_status st = plan_impl(pl, K_host, s);
+  if (st != SSM_OK) {
+    cudaStreamSynchronize(s);
+    release(pl);
+    return st;
+  }
+  *out = pl;
+  return SSM_OK;
+}
+
+ssm_status ssm_solve(ssm_plan_t plan, const float* M_dev, int64_t ldm, float* F_dev, int64_t ldf,
+                     ssm_info* info, void* stream) {
+  if (!plan || !M_dev || !F_dev) {
+    set_error("NULL plan or buffer");
+    return SSM_EINVAL;
+  }
+  if (ldm < plan->g.N || ldf < plan->g.N) {
+    set_error("leading dimension smaller than N");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(plan->device));
+  return solve_impl(plan, M_dev, ldm, F_dev, ldf, info, static_cast<cudaStream_t>(stream));
+}
+
+ssm_status ssm_solve_host(ssm_plan_t plan, const float* M_host, int64_t ldm, float* F_host,
+                          int64_t ldf, ssm_info* info, void* stream) {
+  if (!plan || !M_host || !F_host) {
+    set_error("NULL plan or buffer");
+    return SSM_EINVAL;
+  }
+  if (ldm < plan->g.N || ldf < plan->g.N) {
+    set_error("leading dimension smaller than N");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t ld = plan->g.ld;
+  if (!plan->Mstage) SSM_TRY(dalloc(&plan->Mstage, (size_t)plan->P * ld, s));
+  if (!plan->Fstage) SSM_TRY(dalloc(&plan->Fstage, (size_t)plan->Q * ld, s));
+  SSM_CUDA(cudaMemcpy2DAsync(plan->Mstage, sizeof(float) * ld, M_host, sizeof(float) * ldm,
+                             sizeof(float) * plan->g.N, plan->P, cudaMemcpyHostToDevice, s));
+  ssm_status st = solve_impl(plan, plan->Mstage, ld, plan->Fstage, ld, nullptr, s);
+  if (st != SSM_OK && st != SSM_ENOTCONVERGED) return st;
+  SSM_CUDA(cudaMemcpy2DAsync(F_host, sizeof(float) * ldf, plan->Fstage, sizeof(float) * ld,
+                             sizeof(float) * plan->g.N, plan->Q, cudaMemcpyDeviceToHost, s));
+  SSM_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    // the device-side info of the last solve is not kept; recompute the cheap fields
+    info->status = st;
+    info->rank = plan->r;
+    info->gram_side = plan->gram_side;
+    info->xi_p = plan->xi;
+    info->dtd_norm = plan->dtd_norm;
+    info->sigma1 = plan->sigma1;
+    info->plan_ms = plan->plan_ms;
+    info->iterations = -1;
+    info->res_primal = info->res_change = -1;
+  }
+  return st;
+}
+
+ssm_status ssm_objective(ssm_plan_t plan, const float* M_dev, int64_t ldm, const float* F_dev,
+                         int64_t ldf, int use_full_k, double* J_host, void* stream) {
+  if (!plan || !M_dev || !F_dev || !J_host) {
+    set_error("NULL argument");
+    return SSM_EINVAL;
+  }
+  if (ldm < plan->g.N || ldf < plan->g.N) {
+    set_error("leading dimension smaller than N");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t ld = plan->g.ld;
+  if (!plan->Res) SSM_TRY(dalloc(&plan->Res, (size_t)plan->P * ld, s));
+  SSM_CUDA(cudaMemcpy2DAsync(plan->Res, sizeof(float) * ld, M_dev, sizeof(float) * ldm,
+                             sizeof(float) * plan->g.N, plan->P, cudaMemcpyDeviceToDevice, s));
+  const float* Kd = (use_full_k || plan->p.form == SSM_FORM_DENSE) ? plan->K32 : plan->Kr32;
+  // Res = M - K' F
+  SSM_TRY(sgemm(plan->P, (int)plan->g.N, plan->Q, -1.f, Kd, plan->Q, F_dev, ldf, 1.f, plan->Res,
+                ld, s));
+  int nparts = 0;
+  SSM_TRY(objective_terms(plan, plan->Res, plan->P, F_dev, ldf, plan->red, &nparts, s));
+  SSM_TRY(finish_partials(plan->red, nparts, 2, plan->red_out, s));
+  SSM_CUDA(cudaMemcpyAsync(plan->red_host, plan->red_out, 2 * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+  SSM_CUDA(cudaStreamSynchronize(s));
+  // 1/2 ||R||^2 + lambda * 1/2 ||D F||^2, with 1/2 ||D F||^2 = (s/2) sum_edges (F_n - F_m)^2
+  const double sfac = plan->p.stencil_pairs == 2 ? 1.0 : 0.5;
+  *J_host = 0.5 * plan->red_host[0] + plan->p.lambda * sfac * plan->red_host[1];
+  return SSM_OK;
+}
+
+ssm_status ssm_plan_factors(ssm_plan_t plan, double* sigma_host, double* vr_host, int* rank_out) {
+  if (!plan) {
+    set_error("NULL plan");
+    return SSM_EINVAL;
+  }
+  if (sigma_host) std::memcpy(sigma_host, plan->sigma.data(), sizeof(double) * plan->n);
+  if (rank_out) *rank_out = plan->r;
+  if (vr_host) {
+    // V_r from Kt: K K^T side holds sigma_i v_i, K^T K side holds v_i
+    SSM_CUDA(cudaSetDevice(plan->device));
+    std::vector<double> kt((size_t)plan->Q * plan->n);
+    SSM_CUDA(cudaMemcpy(kt.data(), plan->Kt64, sizeof(double) * kt.size(), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < plan->Q; ++q)
+      for (int i = 0; i < plan->r; ++i) {
+        double v = kt[(size_t)q * plan->n + i];
+        if (plan->gram_side == 0) v = plan->sigma[i] > 0 ? v / plan->sigma[i] : 0.0;
+        vr_host[(size_t)q * plan->r + i] = v;
+      }
+  }
+  return SSM_OK;
+}
+
+ssm_status ssm_destroy(ssm_plan_t plan) {
+  if (!plan) return SSM_OK;
+  cudaSetDevice(plan->device);
+  cudaDeviceSynchronize();
+  release(plan);
+  return SSM_OK;
+}
+
+const char* ssm_status_string(int status) {
+  switch (status) {
+    case SSM_OK: return "ok";
+    case SSM_EINVAL: return "invalid argument";
+    case SSM_ENOMEM: return "out of device memory";
+    case SSM_ECUDA: return "CUDA error";
+    case SSM_ENAN: return "non-finite residual";
+    case SSM_ETIMEOUT: return "device wait timed out";
+    case SSM_EUNSUPPORTED: return "unsupported configuration";
+    case SSM_ENOTCONVERGED: return "tolerance not reached within max_iter";
+    default: return "unknown status";
+  }
+}
+
+const char* ssm_last_error(void) { return t_last_error.c_str(); }
+
+int64_t ssm_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

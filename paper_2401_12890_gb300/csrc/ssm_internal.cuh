@@ -1,0 +1,159 @@
+// Internal declarations shared by the CUDA translation units of the solver library.
+// Nothing here is part of the public ABI (include/ssm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/ssm.h"
+
+namespace ssm {
+
+// ------------------------------------------------------------------------------------
+// error handling: every CUDA call is checked; failures become a status + message
+// ------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+extern std::atomic<int64_t> g_launches;
+
+#define SSM_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      ::ssm::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));              \
+      return e_ == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA;                   \
+    }                                                                                    \
+  } while (0)
+
+#define SSM_LAUNCHED()                                                                   \
+  do {                                                                                   \
+    ::ssm::g_launches.fetch_add(1, std::memory_order_relaxed);                           \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess) {                                                             \
+      ::ssm::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));         \
+      return SSM_ECUDA;                                                                  \
+    }                                                                                    \
+  } while (0)
+
+#define SSM_TRY(expr)                                                                    \
+  do {                                                                                   \
+    ssm_status s_ = (expr);                                                              \
+    if (s_ != SSM_OK) return s_;                                                         \
+  } while (0)
+
+// ------------------------------------------------------------------------------------
+// grid description used by every stencil kernel (Eq. 8, free boundary)
+// ------------------------------------------------------------------------------------
+struct Grid {
+  int nx, ny, nz;     // nz = 1 for 2D, ny = nz = 1 for 1D
+  int64_t N;          // nx*ny*nz
+  int64_t ld;         // leading dimension of every map-major Q x N array (elements)
+};
+
+// the largest padded rank the fused low-rank kernel is instantiated for
+constexpr int kMaxRank = 64;
+
+// ------------------------------------------------------------------------------------
+// the plan (opaque ssm_plan_t)
+// ------------------------------------------------------------------------------------
+}  // namespace ssm
+
+struct ssm_plan_s {
+  ssm_params p;
+  int device = 0;
+  ssm::Grid g{};
+  int P = 0, Q = 0, n = 0;     // n = min(P, Q): size of the Gram eigenproblem
+  int gram_side = 0;           // 0: K K^T, 1: K^T K
+  int r = 0, R = 0;            // rank used, padded rank (multiple of 4)
+  double xi = 0, dtd_norm = 0, sigma1 = 0, lam_s = 0;
+  std::vector<double> sigma;   // n singular values, descending
+  std::vector<int> perm;       // eigen order (descending) into the Jacobi output
+  float plan_ms = 0.f;
+
+  // FP64 plan data
+  double* K64 = nullptr;       // P x Q
+  double* Bp64 = nullptr;      // P x n  : c = Bp^T m (u_i, or K v_i)
+  double* Kt64 = nullptr;      // Q x n  : k_i = K^T u_i (KK^T side) or v_i (K^TK side)
+  double* sig64 = nullptr;     // n      : sigma_i (descending)
+
+  // FP32 operands
+  float* K32 = nullptr;        // P x Q (objective with the full K)
+  float* Kr32 = nullptr;       // P x Q (objective with K_r)
+  float* V32 = nullptr;        // Q x R  [q][i]  low-rank right singular vectors
+  float* coefA = nullptr;      // R      1/(beta + sigma_i^2)
+  float* coefW = nullptr;      // R      sigma_i^2/(beta^2 + beta sigma_i^2)
+  double* alpha64 = nullptr;   // n      S_i = alpha_i c_i
+  float* Mq32 = nullptr;       // Q x Q  (K^T K + beta I)^{-1}, row stride Qp
+  __nv_bfloat16* Mhi = nullptr;  // Q x Qp (bf16 split of Mq: hi + lo)
+  __nv_bfloat16* Mlo = nullptr;
+  float* Gq32 = nullptr;       // Q x n  : h = Gq c
+  int Qp = 0;                  // padded row stride of Q x Q operands
+
+  // per-voxel state (map-major, leading dimension g.ld)
+  float* Z[2] = {nullptr, nullptr};  // z ping-pong            (Q x ld)
+  float* Dl[2] = {nullptr, nullptr}; // dual d ping-pong       (Q x ld)
+  float* C32 = nullptr;              // projections c          (n x ld)
+  float* S = nullptr;                // S_i = sigma_i u_i^T m  (R x ld)
+  float* U[2] = {nullptr, nullptr};  // u = V^T (beta z - d)   (R x ld)
+  float* H = nullptr;                // h = M g                (Q x ld)     dense
+  float* Wf = nullptr;               // w = beta z - d (FP32)  (Q x ld)     dense fp32
+  float* Acc = nullptr;              // M w                    (Q x ld)     dense fp32
+  __nv_bfloat16* Whi[2] = {nullptr, nullptr};  // w split, ping-pong (Q x ld) dense bf16
+  __nv_bfloat16* Wlo[2] = {nullptr, nullptr};
+  float* Res = nullptr;              // P x ld residual buffer for the objective (lazy)
+  float* Mstage = nullptr;           // P x ld device staging for ssm_solve_host (lazy)
+  float* Fstage = nullptr;           // Q x ld
+  double* red = nullptr;             // reduction partials
+  double* red_out = nullptr;         // finished sums (device)
+  double* red_host = nullptr;        // pinned host copy
+  int red_cap = 0;                   // capacity (rows of 4 doubles)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  void* tc_state = nullptr;          // tensor-core path descriptors (ssm_tc.cu)
+};
+
+namespace ssm {
+
+// ------------------------------------------------------------------------------------
+// launchers (each returns a status; the stream is the caller's)
+// ------------------------------------------------------------------------------------
+// plan stage (ssm_plan_kernels.cu)
+ssm_status gram_fp64(const double* K, int P, int Q, int side, double* A, cudaStream_t s);
+ssm_status jacobi_eigen(double* A, int n, double* E, double* scratch, std::vector<double>& evals,
+                        cudaStream_t s);
+ssm_status factors_fp64(ssm_plan_s* pl, const double* E, cudaStream_t s);
+ssm_status form_dense_inverse(ssm_plan_s* pl, cudaStream_t s);
+ssm_status project_data(const ssm_plan_s* pl, const float* M, int64_t ldm, int ncomp,
+                        cudaStream_t s);
+ssm_status split_bf16(const float* X, int rows, int cols, int64_t ldx,
+                      __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, cudaStream_t s);
+
+// low-rank iteration (ssm_lowrank.cu)
+ssm_status lowrank_iteration(ssm_plan_s* pl, int cur, bool check, double* partial,
+                             int* nparts, cudaStream_t s);
+int lowrank_max_partials(const ssm_plan_s* pl);
+
+// dense iteration and shared kernels (ssm_dense.cu)
+ssm_status sgemm(int M, int N, int K, float alpha, const float* A, int64_t lda,
+                 const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                 cudaStream_t s);
+ssm_status dense_update(ssm_plan_s* pl, int cur, const float* acc, bool check,
+                        bool write_fp32_w, bool write_bf16_w, double* partial, int* nparts,
+                        cudaStream_t s);
+int dense_max_partials(const ssm_plan_s* pl);
+ssm_status finish_partials(const double* partial, int nparts, int width, double* out,
+                           cudaStream_t s);
+ssm_status objective_terms(const ssm_plan_s* pl, const float* Res, int P, const float* F,
+                           int64_t ldf, double* partial, int* nparts, cudaStream_t s);
+
+// tensor-core dense iteration (ssm_tc.cu)
+ssm_status tc_prepare(ssm_plan_s* pl, cudaStream_t s);
+ssm_status tc_iteration(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
+                        cudaStream_t s);
+void tc_release(ssm_plan_s* pl);
+int tc_max_partials(const ssm_plan_s* pl);
+
+}  // namespace ssm

@@ -1,0 +1,214 @@
+"""Thin ctypes binding of the C ABI in include/ssm.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library (libssm.so, built by
+paper_2401_12890_gb300.build). Importing this module does not need a GPU; creating a
+Plan does, and raises if the library is missing -- there is no CPU fallback.
+
+    plan = Plan(K, dims=(128, 128), lam=1e-2, beta=0.99, form="dense", precision="bf16x3")
+    F, info = plan.solve(M_gpu)          # M: torch.cuda float32 tensor P x N
+    plan.close()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libssm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ssm.h")
+
+SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENAN, SSM_ETIMEOUT, SSM_EUNSUPPORTED, \
+    SSM_ENOTCONVERGED = range(8)
+FORMS = {"lowrank": 0, "dense": 1}
+PRECISIONS = {"fp32": 0, "bf16x3": 1}
+
+
+class SsmParams(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("P", ctypes.c_int),
+        ("Q", ctypes.c_int), ("lam", ctypes.c_double), ("beta", ctypes.c_double),
+        ("xi_p", ctypes.c_double), ("form", ctypes.c_int), ("rank", ctypes.c_int),
+        ("rank_tol", ctypes.c_double), ("precision", ctypes.c_int),
+        ("stencil_pairs", ctypes.c_int), ("max_iter", ctypes.c_int),
+        ("check_every", ctypes.c_int), ("tol_primal", ctypes.c_double),
+        ("tol_change", ctypes.c_double),
+    ]
+
+
+class SsmInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("iterations", ctypes.c_int), ("rank", ctypes.c_int),
+        ("gram_side", ctypes.c_int), ("xi_p", ctypes.c_double), ("dtd_norm", ctypes.c_double),
+        ("sigma1", ctypes.c_double), ("res_primal", ctypes.c_double),
+        ("res_change", ctypes.c_double), ("plan_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+class SsmError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load_library()
+        msg = lib.ssm_status_string(status).decode()
+        detail = lib.ssm_last_error().decode()
+        super().__init__(f"{where}: {msg} ({detail})")
+        self.status = status
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the functions include/ssm.h declares."""
+    text = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\*]+\s+)+\*?(ssm_\w+)\s*\(", text, re.M)))
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libssm.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library {path} is missing: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, i64, dp, fp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+    lib.ssm_default_params.argtypes = [ctypes.POINTER(SsmParams)]
+    lib.ssm_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SsmParams), vp, ctypes.c_int, vp]
+    lib.ssm_solve.argtypes = [vp, fp, i64, fp, i64, ctypes.POINTER(SsmInfo), vp]
+    lib.ssm_solve_host.argtypes = [vp, fp, i64, fp, i64, ctypes.POINTER(SsmInfo), vp]
+    lib.ssm_objective.argtypes = [vp, fp, i64, fp, i64, ctypes.c_int, dp, vp]
+    lib.ssm_plan_factors.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
+    lib.ssm_destroy.argtypes = [vp]
+    lib.ssm_status_string.argtypes = [ctypes.c_int]
+    lib.ssm_status_string.restype = ctypes.c_char_p
+    lib.ssm_last_error.restype = ctypes.c_char_p
+    lib.ssm_launch_count.restype = ctypes.c_int64
+    for name in ("ssm_default_params", "ssm_plan", "ssm_solve", "ssm_solve_host",
+                 "ssm_objective", "ssm_plan_factors", "ssm_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def launch_count() -> int:
+    return int(load_library().ssm_launch_count())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A planned solver for one dictionary K (P x Q) and one voxel grid."""
+
+    def __init__(self, K, dims, lam, beta, *, form="lowrank", precision="fp32", rank=0,
+                 rank_tol=5e-5, xi_p=0.0, stencil_pairs=2, max_iter=300, check_every=10,
+                 tol_primal=0.0, tol_change=0.0, device=0, stream=None):
+        lib = load_library()
+        K = np.ascontiguousarray(K, dtype=np.float64)
+        p = SsmParams()
+        lib.ssm_default_params(ctypes.byref(p))
+        dims = tuple(int(d) for d in dims)
+        p.ndim = len(dims)
+        for i, d in enumerate(dims):
+            p.dims[i] = d
+        p.P, p.Q = int(K.shape[0]), int(K.shape[1])
+        p.lam, p.beta, p.xi_p = float(lam), float(beta), float(xi_p)
+        p.form = FORMS[form]
+        p.precision = PRECISIONS[precision]
+        p.rank, p.rank_tol = int(rank), float(rank_tol)
+        p.stencil_pairs = int(stencil_pairs)
+        p.max_iter, p.check_every = int(max_iter), int(check_every)
+        p.tol_primal, p.tol_change = float(tol_primal), float(tol_change)
+        self.params = p
+        self.dims = dims
+        self.P, self.Q = p.P, p.Q
+        self.N = int(np.prod(dims))
+        self.device = device
+        self._h = ctypes.c_void_p()
+        st = lib.ssm_plan(ctypes.byref(self._h), ctypes.byref(p),
+                          K.ctypes.data_as(ctypes.c_void_p), int(device), _stream_handle(stream))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_plan")
+
+    def solve(self, M, out=None, stream=None):
+        """M: CUDA float32 tensor P x N (row stride >= N). Returns (F tensor Q x N, info)."""
+        import torch
+        assert M.is_cuda and M.dtype == torch.float32 and M.dim() == 2 and M.stride(1) == 1
+        assert M.shape[0] == self.P and M.shape[1] == self.N
+        if out is None:
+            out = torch.empty((self.Q, self.N), dtype=torch.float32, device=M.device)
+        info = SsmInfo()
+        st = load_library().ssm_solve(self._h, ctypes.c_void_p(M.data_ptr()), M.stride(0),
+                                      ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                                      ctypes.byref(info), _stream_handle(stream))
+        if st not in (SSM_OK, SSM_ENOTCONVERGED):
+            raise SsmError(st, "ssm_solve")
+        return out, info.as_dict()
+
+    def solve_async(self, M, out, stream=None):
+        """As solve() without the info read-back (no host synchronisation unless a
+        tolerance test needs it). Returns the status."""
+        st = load_library().ssm_solve(self._h, ctypes.c_void_p(M.data_ptr()), M.stride(0),
+                                      ctypes.c_void_p(out.data_ptr()), out.stride(0), None,
+                                      _stream_handle(stream))
+        if st not in (SSM_OK, SSM_ENOTCONVERGED):
+            raise SsmError(st, "ssm_solve")
+        return st
+
+    def solve_host(self, M_host, F_host, stream=None):
+        """Host buffers (torch CPU tensors, pinned for async copies). Returns the status."""
+        st = load_library().ssm_solve_host(self._h, ctypes.c_void_p(M_host.data_ptr()),
+                                           M_host.stride(0), ctypes.c_void_p(F_host.data_ptr()),
+                                           F_host.stride(0), None, _stream_handle(stream))
+        if st not in (SSM_OK, SSM_ENOTCONVERGED):
+            raise SsmError(st, "ssm_solve_host")
+        return st
+
+    def objective(self, M, F, use_full_k=False, stream=None):
+        J = ctypes.c_double()
+        st = load_library().ssm_objective(self._h, ctypes.c_void_p(M.data_ptr()), M.stride(0),
+                                          ctypes.c_void_p(F.data_ptr()), F.stride(0),
+                                          int(bool(use_full_k)), ctypes.byref(J),
+                                          _stream_handle(stream))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_objective")
+        return J.value
+
+    def factors(self, with_vr=True):
+        n = min(self.P, self.Q)
+        sig = np.zeros(n)
+        r = ctypes.c_int()
+        load_library().ssm_plan_factors(self._h, sig.ctypes.data_as(ctypes.c_void_p), None,
+                                        ctypes.byref(r))
+        vr = None
+        if with_vr:
+            vr = np.zeros((self.Q, r.value))
+            st = load_library().ssm_plan_factors(self._h, None,
+                                                 vr.ctypes.data_as(ctypes.c_void_p), None)
+            if st != SSM_OK:
+                raise SsmError(st, "ssm_plan_factors")
+        return sig, vr, r.value
+
+    def close(self):
+        if self._h:
+            load_library().ssm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
