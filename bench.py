@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Benchmark of the LADMM solver on one GB300 (or N replicas under torchrun).
+
+Metric: voxel x compartment x iterations per second of the LADMM iteration
+(Algorithm 2), plus time to tolerance (p50/p99), per precision form, on the 2D
+diffusion-relaxation slice workload: 128 x 128 voxels (N = 16384), P = 120 encodings
+(15 b-values x 8 echo times), Q = 2500 compartments (50 x 50 log-spaced D x T2),
+lambda = 1e-2, synthetic seeded data (SNR 100).
+
+A step is one ssm_solve: the data projections (Algorithm 2, step 4), ITERS_PER_STEP
+iterations of steps 6-11 with the residual test every 10 iterations, and the copy of
+z into F. The plan (steps 1-3: Gram, eigendecomposition, rank, weights) is built once
+per dictionary before the timed region; its time is reported as plan_ms.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own independent problem (a different seed) with
+no collective on the data path: weak scaling, value = all ranks' work / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "dr2d_slice"
+ITERS_PER_STEP = 100
+CHECK_EVERY = 10
+TTT_TOL = 3e-4
+METRIC = "voxel*compartment*iters/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="auto",
+                    help="headline form: lowrank_fp32 | dense_fp32 | dense_bf16x3 | auto")
+    ap.add_argument("--ttt-repeats", type=int, default=7)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline form only")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = [ln.split(",") for ln in open(self.tmp.name).read().splitlines() if ln.strip()]
+        os.unlink(self.tmp.name)
+        sms, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sms.append(float(r[1]))
+                mx.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sms:
+            out = {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(mx),
+                   "reasons": sorted(reasons), "samples": len(sms),
+                   "power_w_max": max(power) if power else None}
+        return out
+
+
+# --------------------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def traffic_record(kernel_file, kernel_name):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is
+    unchanged since the capture (profiles/traffic.json records its hash)."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel_name]
+    except (OSError, ValueError, KeyError):
+        return None
+    src = os.path.join(ROOT, "paper_2401_12890_gb300", "csrc", kernel_file)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha") != h:
+        return None
+    return rec.get("dram_bytes_per_launch_full")
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Dist:
+    def __init__(self, backend):
+        self.world, self.rank, self.local = dist_env()
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v):
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+FORMS = [("lowrank", "fp32"), ("dense", "bf16x3"), ("dense", "fp32")]
+
+
+def form_key(form, prec):
+    return f"{form}_{prec}"
+
+
+def dominant_kernel(form, prec, Q, N, r):
+    """(kernel name, source file, bound, algorithmic amount per launch, unit)."""
+    if form == "lowrank":
+        # read z and write z' per state element (d cancels from the iteration, see
+        # ssm_lowrank.cu); read S, u and write u' per voxel
+        return ("lowrank_iter_kernel", "ssm_lowrank.cu", "hbm",
+                8.0 * Q * N + 12.0 * r * N, "GB/s")
+    if prec == "fp32":
+        return ("sgemm_kernel", "ssm_dense.cu", "alu", 2.0 * Q * Q * N, "TFLOP/s")
+    return ("tc_dense_kernel", "ssm_tc.cu", "tensor", 3 * 2.0 * Q * Q * N, "TFLOP/s")
+
+
+# --------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------
+def bench_ours(args):
+    import torch
+
+    import __graft_entry__
+    from paper_2401_12890_gb300 import ssm, synth
+
+    dist = Dist("nccl")
+    torch.cuda.set_device(dist.local)
+    if dist.rank == 0:
+        __graft_entry__.build()
+    dist.barrier()
+    ssm.load_library()
+    w = synth.WORKLOADS[WORKLOAD]
+    K, M, _ = synth.make_problem(WORKLOAD, seed=w.seed + 7919 * dist.rank)
+    N, Q, P = w.N, w.Q, w.P
+    Md = torch.from_numpy(M).cuda()
+    F = torch.empty((Q, N), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def make_plan(form, prec, **kw):
+        base = dict(form=form, precision=prec, max_iter=ITERS_PER_STEP, check_every=CHECK_EVERY)
+        base.update(kw)
+        return ssm.Plan(K, w.dims, w.lam, w.beta, **base)
+
+    # which forms this build offers
+    available = []
+    for form, prec in FORMS:
+        try:
+            pl = make_plan(form, prec, max_iter=1)
+            pl.close()
+            available.append((form, prec))
+        except ssm.SsmError as e:
+            if e.status != ssm.SSM_EUNSUPPORTED:
+                raise
+    if args.form == "auto":
+        head = ("dense", "bf16x3") if ("dense", "bf16x3") in available else available[0]
+    else:
+        f, p = args.form.split("_")
+        head = (f, p)
+    forms_to_run = [head] if args.quick else [head] + [fp for fp in available if fp != head]
+
+    results = {}
+    headline = None
+    for form, prec in forms_to_run:
+        key = form_key(form, prec)
+        plan = make_plan(form, prec)
+        steps = args.steps if (form, prec) == head else max(2, min(3, args.steps))
+        warm = args.warmup if (form, prec) == head else 1
+        for _ in range(warm):
+            plan.solve_async(Md, F)
+        torch.cuda.synchronize()
+        plan.profile(True)
+        plan.profile_read()
+        launches0 = ssm.launch_count()
+        clocks = ClockSampler(dist.local)
+        dist.barrier()
+        torch.cuda.synchronize()
+        if (form, prec) == head:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_" + key)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.solve_async(Md, F)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        dist.barrier()
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop() if (form, prec) == head else None
+        launches = ssm.launch_count() - launches0
+        kms, kl = plan.profile_read()
+        plan.profile(False)
+        ms_max = dist.max(ms)
+        per_step = ms_max / steps
+        value = dist.world * N * Q * ITERS_PER_STEP / (per_step / 1e3)
+        info = plan.solve(Md, F)[1]
+        rec = {"value": value, "ms_per_step": per_step,
+               "us_per_iteration": 1e3 * per_step / ITERS_PER_STEP,
+               "rank": info["rank"], "gpu_launches": launches,
+               "main_kernel_ms_avg": kms / max(kl, 1), "main_kernel_launches": kl}
+        # time to tolerance: fresh solves to ||z-f|| and ||dz|| <= TTT_TOL ||z||
+        tplan = make_plan(form, prec, max_iter=20000, tol_primal=TTT_TOL, tol_change=TTT_TOL)
+        tplan.solve(Md, F)
+        reps = args.ttt_repeats if (form, prec) == head else 3
+        if form == "dense" and prec == "fp32":
+            reps = 2
+        times, iters = [], []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, tinfo = tplan.solve(Md, F)
+            torch.cuda.synchronize()
+            times.append(1e3 * (time.perf_counter() - t0))
+            iters.append(tinfo["iterations"])
+        tplan.close()
+        rec["time_to_tol_ms"] = {"tol": TTT_TOL, "p50": float(np.percentile(times, 50)),
+                                 "p99": float(np.percentile(times, 99)),
+                                 "iterations": int(statistics.median(iters)),
+                                 "samples": len(times)}
+        results[key] = rec
+        if (form, prec) == head:
+            kname, kfile, bound, amount, unit = dominant_kernel(form, prec, Q, N, info["rank"])
+            avg_s = kms / max(kl, 1) / 1e3
+            pk = measured_peaks()
+            if bound == "hbm":
+                peak = pk["hbm_gbs"] if pk else 6800.0
+                achieved = amount / avg_s / 1e9
+                peak_src = "of measured hbm_gbs" if pk else "of fallback 6.8 TB/s"
+            elif bound == "tensor":
+                peak = pk["bf16_tflops_sustained"] if pk else 1700.0
+                achieved = amount / avg_s / 1e12
+                peak_src = "of measured bf16_tflops_sustained" if pk else "of fallback"
+            else:
+                # FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
+                mhz = (pk or {}).get("sm_max_mhz", 2070.0)
+                peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+                achieved = amount / avg_s / 1e12
+                peak_src = "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"
+            traffic = traffic_record(kfile, kname)
+            headline = {
+                "rec": rec, "clocks": clk, "launches": launches,
+                "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
+                             "unit": unit, "frac": achieved / peak, "peak_source": peak_src,
+                             "traffic": traffic,
+                             "algorithmic_per_launch": amount},
+            }
+            # end to end through the C ABI with host buffers (pinned), copies timed
+            Mh = torch.from_numpy(M).pin_memory()
+            Fh = torch.empty((Q, N), dtype=torch.float32).pin_memory()
+            plan.solve_host(Mh, Fh)
+            e2e_times = []
+            dist.barrier()
+            for _ in range(max(2, min(args.steps, 5))):
+                t0 = time.perf_counter()
+                plan.solve_host(Mh, Fh)
+                e2e_times.append(time.perf_counter() - t0)
+            e2e_s = dist.max(statistics.median(e2e_times))
+            headline["e2e"] = {"value": dist.world * N * Q * ITERS_PER_STEP / e2e_s,
+                               "unit": METRIC, "h2d_bytes_per_step": int(P * N * 4),
+                               "d2h_bytes_per_step": int(Q * N * 4)}
+            headline["plan_ms"] = info["plan_ms"]
+        plan.close()
+
+    # CPU baseline: the FP64 oracle as it stands, a bounded sample of this workload,
+    # and the error of each GPU form after the same iteration count
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_and_errors(K, M, w, Md, F, make_plan, forms_to_run)
+
+    if dist.rank == 0:
+        hl = headline
+        out = {
+            "metric": METRIC, "value": hl["rec"]["value"], "unit": METRIC,
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": hl["rec"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if head[1] == "fp32" else "bf16x3+f32",
+            "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: 2D diffusion-relaxation slice 128x128 "
+                                   f"(N={N}), P={P}, Q={Q}, lambda={w.lam}, beta={w.beta:.4g}",
+                       "form": form_key(*head), "iters_per_step": ITERS_PER_STEP,
+                       "check_every": CHECK_EVERY, "rank": hl["rec"]["rank"],
+                       "plan_ms": hl["plan_ms"],
+                       "l2": "inputs larger than L2 (each Q x N state array is 164 MB)",
+                       "parallelism": f"replicas x{dist.world}"},
+            "clocks": hl["clocks"], "e2e": hl["e2e"], "gpu_launches": hl["launches"],
+            "roofline": hl["roofline"], "cpu_baseline": cpu and cpu["baseline"],
+            "time_to_tol_ms": hl["rec"]["time_to_tol_ms"],
+            "forms": results,
+            "err_vs_oracle": cpu and cpu["errors"],
+        }
+        print(json.dumps(out), flush=True)
+    dist.close()
+
+
+def cpu_baseline_and_errors(K, M, w, Md, F, make_plan, forms):
+    from oracle import ladmm as L
+    iters = 3
+    t0 = time.perf_counter()
+    ref = L.ladmm(K, M, w.dims, w.lam, w.beta, iters=iters, check_every=0)
+    dt = time.perf_counter() - t0
+    baseline = {"value": w.N * w.Q * iters / dt, "unit": METRIC, "cores": os.cpu_count(),
+                "kind": "oracle",
+                "sample": f"FP64 numpy oracle, low-rank Algorithm 2 (r={ref['r']}), full "
+                          f"{WORKLOAD} inputs, setup + {iters} iterations ({dt:.1f} s); "
+                          "numpy's default BLAS threading"}
+    errors = {}
+    refd = None
+    for form, prec in forms:
+        if form == "dense" and refd is None:
+            refd = L.ladmm(K, M, w.dims, w.lam, w.beta, dense=True, iters=iters, check_every=0)
+        pl = make_plan(form, prec, max_iter=iters, check_every=0)
+        out, _ = pl.solve(Md, F)
+        z = out.cpu().numpy().astype(np.float64)
+        pl.close()
+        zr = (refd if form == "dense" else ref)["z"]
+        errors[form_key(form, prec)] = {
+            "iterations": iters,
+            "rel_fro": float(np.linalg.norm(z - zr) / np.linalg.norm(zr))}
+    return {"baseline": baseline, "errors": errors}
+
+
+# --------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle itself on the host cores
+# --------------------------------------------------------------------------------------
+def bench_reference(args):
+    world, rank, _ = dist_env()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group(backend="gloo")
+        if rank != 0:
+            tdist.destroy_process_group()
+            return
+    from oracle import ladmm as L
+    from paper_2401_12890_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    K, M, _ = synth.make_problem(WORKLOAD)
+    iters = 1
+    for _ in range(args.warmup):
+        L.ladmm(K, M, w.dims, w.lam, w.beta, iters=iters, check_every=0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.ladmm(K, M, w.dims, w.lam, w.beta, iters=iters, check_every=0)
+    dt = time.perf_counter() - t0
+    value = w.N * w.Q * iters * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 2D diffusion-relaxation slice 128x128 "
+                               f"(N={w.N}), P={w.P}, Q={w.Q}, lambda={w.lam}",
+                   "form": "lowrank (Algorithm 2) FP64 oracle"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"each step: oracle setup (SVD, g) + {iters} iteration(s) "
+                                   "on the full workload"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -160,6 +160,19 @@ ssm_status ssm_objective(ssm_plan_t plan, const float* M_dev, int64_t ldm,
 ssm_status ssm_plan_factors(ssm_plan_t plan, double* sigma_host, double* vr_host,
                             int* rank_out);
 
+/*
+ * Kernel timing (measurement support, no counterpart in the paper). When enabled,
+ * each solve records a CUDA event pair on `stream` around every launch of the
+ * iteration's dominant kernel (the fused low-rank kernel, the FP32 matrix product,
+ * or the tensor-core kernel) and ssm_profile_read returns the summed device time
+ * (ms) and launch count since the last read (then resets them; synchronises the
+ * plan's device). Disabled by default; enabling costs two event records per
+ * iteration.
+ */
+ssm_status ssm_profile_enable(ssm_plan_t plan, int enable);
+ssm_status ssm_profile_read(ssm_plan_t plan, double* main_kernel_ms,
+                            int64_t* main_kernel_launches);
+
 /* Free everything the plan owns. NULL is accepted. Synchronises the plan's device. */
 ssm_status ssm_destroy(ssm_plan_t plan);
 

@@ -6,7 +6,10 @@
 #include <cstring>
 #include <numeric>
 
+#include <cudaTypedefs.h>
+
 #include "ssm_internal.cuh"
+#include "ssm_tma.cuh"
 
 namespace ssm {
 
@@ -14,6 +17,35 @@ std::atomic<int64_t> g_launches{0};
 static thread_local std::string t_last_error;
 
 void set_error(const std::string& msg) { t_last_error = msg; }
+
+cudaError_t encode_2d(CUtensorMap* map, CUtensorMapDataType dtype, size_t elem, const void* base,
+                      uint64_t cols, uint64_t rows, uint64_t ld, unsigned box_cols,
+                      unsigned box_rows, CUtensorMapSwizzle swizzle) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+      set_error("cuTensorMapEncodeTiled is not available from the driver");
+      return e != cudaSuccess ? e : cudaErrorNotSupported;
+    }
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * elem};
+  cuuint32_t box[2] = {box_cols, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
 
 namespace {
 
@@ -67,8 +99,8 @@ ssm_status validate(const ssm_params* p) {
     }
     N *= p->dims[d];
   }
-  if (N > ((int64_t)1 << 34)) {
-    set_error("too many voxels");
+  if (N > ((int64_t)1 << 31) - 4096) {
+    set_error("too many voxels (at most 2^31 - 4096: TMA coordinates are 32-bit)");
     return SSM_EINVAL;
   }
   if (p->P < 1 || p->Q < 1 || p->P > 65536 || p->Q > 65536) {
@@ -136,9 +168,11 @@ void release(ssm_plan_s* pl) {
   dfree(pl->Fstage);
   dfree(pl->red);
   dfree(pl->red_out);
+  dfree(pl->dev_err);
   if (pl->red_host) cudaFreeHost(pl->red_host);
   if (pl->ev0) cudaEventDestroy(pl->ev0);
   if (pl->ev1) cudaEventDestroy(pl->ev1);
+  for (cudaEvent_t e : pl->prof_ev) cudaEventDestroy(e);
   delete pl;
 }
 
@@ -253,7 +287,9 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   int maxparts = 1;
   if (p.form == SSM_FORM_LOWRANK) {
     SSM_TRY(dalloc(&pl->S, (size_t)pl->R * pl->g.ld, s));
-    for (int i = 0; i < 2; ++i) SSM_TRY(dalloc(&pl->U[i], (size_t)pl->R * pl->g.ld, s));
+    pl->lr_grid = lowrank_grid(pl);
+    const size_t pf = (size_t)lowrank_partial_floats(pl, pl->lr_grid);
+    for (int i = 0; i < 2; ++i) SSM_TRY(dalloc(&pl->U[i], pf, s));
     maxparts = lowrank_max_partials(pl);
   } else {
     SSM_TRY(dalloc(&pl->C32, (size_t)n * pl->g.ld, s));
@@ -275,6 +311,8 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   pl->red_cap = maxparts;
   SSM_TRY(dalloc(&pl->red, (size_t)maxparts * 4, s));
   SSM_TRY(dalloc(&pl->red_out, 4, s));
+  SSM_TRY(dalloc(&pl->dev_err, 1, s));
+  SSM_CUDA(cudaMemsetAsync(pl->dev_err, 0, sizeof(int), s));
   SSM_CUDA(cudaMallocHost(&pl->red_host, 4 * sizeof(double)));
   SSM_CUDA(cudaEventRecord(pl->ev1, s));
   SSM_CUDA(cudaEventSynchronize(pl->ev1));
@@ -283,11 +321,28 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
 }
 
 // residual test: returns (rp, rc) from the three FP64 sums
+// a kernel's bounded wait gave up: report it once and clear the word
+ssm_status check_device_error(ssm_plan_s* pl, int host_err) {
+  if (host_err != 0) {
+    set_error("a device-side wait timed out (bounded mbarrier wait)");
+    return (ssm_status)host_err;
+  }
+  return SSM_OK;
+}
+
 ssm_status read_residuals(ssm_plan_s* pl, int nparts, cudaStream_t s, double* rp, double* rc) {
   SSM_TRY(finish_partials(pl->red, nparts, 3, pl->red_out, s));
   SSM_CUDA(cudaMemcpyAsync(pl->red_host, pl->red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                            s));
+  int* herr = reinterpret_cast<int*>(pl->red_host + 3);
+  SSM_CUDA(cudaMemcpyAsync(herr, pl->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   SSM_CUDA(cudaStreamSynchronize(s));
+  if (*herr != 0) {
+    const int e = *herr;
+    *herr = 0;
+    SSM_CUDA(cudaMemsetAsync(pl->dev_err, 0, sizeof(int), s));
+    return check_device_error(pl, e);
+  }
   const double zn = std::max(pl->red_host[2], 1e-300);
   *rp = std::sqrt(pl->red_host[0] / zn);
   *rc = std::sqrt(pl->red_host[1] / zn);
@@ -299,16 +354,37 @@ ssm_status read_residuals(ssm_plan_s* pl, int nparts, cudaStream_t s, double* rp
   return SSM_OK;
 }
 
-ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, int* nparts, cudaStream_t s) {
+// event pair around the dominant kernel of an iteration (profiling mode only)
+ssm_status prof_mark(ssm_plan_s* pl, bool start, cudaStream_t s) {
+  if (!pl->prof_enabled) return SSM_OK;
+  const size_t idx = 2 * pl->prof_used + (start ? 0 : 1);
+  while (pl->prof_ev.size() <= idx) {
+    cudaEvent_t e;
+    SSM_CUDA(cudaEventCreate(&e));
+    pl->prof_ev.push_back(e);
+  }
+  SSM_CUDA(cudaEventRecord(pl->prof_ev[idx], s));
+  if (!start) ++pl->prof_used;
+  return SSM_OK;
+}
+
+ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, bool check_next, int* nparts,
+                         cudaStream_t s) {
   const ssm_params& p = pl->p;
-  if (p.form == SSM_FORM_LOWRANK) return lowrank_iteration(pl, cur, check, pl->red, nparts, s);
+  SSM_TRY(prof_mark(pl, true, s));
+  if (p.form == SSM_FORM_LOWRANK) {
+    SSM_TRY(lowrank_iteration(pl, cur, check, check_next, pl->red, nparts, s));
+    return prof_mark(pl, false, s);
+  }
   if (p.precision == SSM_FP32) {
     // acc = M w (w^0 = 0, so the first product is 0)
     SSM_TRY(sgemm(pl->Q, (int)pl->g.N, pl->Q, 1.f, pl->Mq32, pl->Qp, pl->Wf, pl->g.ld, 0.f,
                   pl->Acc, pl->g.ld, s));
+    SSM_TRY(prof_mark(pl, false, s));
     return dense_update(pl, cur, pl->Acc, check, true, false, pl->red, nparts, s);
   }
-  return tc_iteration(pl, cur, check, pl->red, nparts, s);
+  SSM_TRY(tc_iteration(pl, cur, check, pl->red, nparts, s));
+  return prof_mark(pl, false, s);
 }
 
 ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int64_t ldf,
@@ -322,7 +398,8 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
     if (pl->R > pl->r)
       SSM_CUDA(cudaMemsetAsync(pl->S + (size_t)pl->r * ld, 0,
                                sizeof(float) * (size_t)(pl->R - pl->r) * ld, s));
-    SSM_CUDA(cudaMemsetAsync(pl->U[0], 0, sizeof(float) * (size_t)pl->R * ld, s));
+    SSM_CUDA(cudaMemsetAsync(
+        pl->U[0], 0, sizeof(float) * (size_t)lowrank_partial_floats(pl, pl->lr_grid), s));
   } else {
     SSM_TRY(project_data(pl, M, ldm, pl->n, s));
     // h = M g = sum_i Gq_i c_i
@@ -343,12 +420,17 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
   double rp = -1, rc = -1;
   ssm_status result = SSM_OK;
   bool converged = false;
+  // iteration j forms the residual sums when it ends on a test boundary or is the last
+  auto is_check = [&](int j) {
+    if (j >= p.max_iter) return false;
+    const bool at = p.check_every > 0 && ((j + 1) % p.check_every == 0);
+    return (use_tol && at) || j + 1 == p.max_iter;
+  };
   while (k < p.max_iter) {
-    const bool last = (k + 1 == p.max_iter);
     const bool at_check = p.check_every > 0 && ((k + 1) % p.check_every == 0);
-    const bool check = (use_tol && at_check) || last;
+    const bool check = is_check(k);
     int nparts = 0;
-    SSM_TRY(one_iteration(pl, cur, check, &nparts, s));
+    SSM_TRY(one_iteration(pl, cur, check, is_check(k + 1), &nparts, s));
     cur ^= 1;
     ++k;
     if (check) {
@@ -537,6 +619,34 @@ ssm_status ssm_plan_factors(ssm_plan_t plan, double* sigma_host, double* vr_host
         vr_host[(size_t)q * plan->r + i] = v;
       }
   }
+  return SSM_OK;
+}
+
+ssm_status ssm_profile_enable(ssm_plan_t plan, int enable) {
+  if (!plan) {
+    set_error("NULL plan");
+    return SSM_EINVAL;
+  }
+  plan->prof_enabled = enable != 0;
+  return SSM_OK;
+}
+
+ssm_status ssm_profile_read(ssm_plan_t plan, double* main_kernel_ms, int64_t* launches) {
+  if (!plan) {
+    set_error("NULL plan");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(plan->device));
+  double total = 0.0;
+  for (size_t i = 0; i < plan->prof_used; ++i) {
+    SSM_CUDA(cudaEventSynchronize(plan->prof_ev[2 * i + 1]));
+    float ms = 0.f;
+    SSM_CUDA(cudaEventElapsedTime(&ms, plan->prof_ev[2 * i], plan->prof_ev[2 * i + 1]));
+    total += ms;
+  }
+  if (main_kernel_ms) *main_kernel_ms = total;
+  if (launches) *launches = (int64_t)plan->prof_used;
+  plan->prof_used = 0;
   return SSM_OK;
 }
 

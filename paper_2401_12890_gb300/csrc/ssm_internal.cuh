@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ssm.h"
+#include "ssm.h"
 
 namespace ssm {
 
@@ -98,7 +98,8 @@ struct ssm_plan_s {
   float* Dl[2] = {nullptr, nullptr}; // dual d ping-pong       (Q x ld)
   float* C32 = nullptr;              // projections c          (n x ld)
   float* S = nullptr;                // S_i = sigma_i u_i^T m  (R x ld)
-  float* U[2] = {nullptr, nullptr};  // u = V^T (beta z - d)   (R x ld)
+  float* U[2] = {nullptr, nullptr};  // partial u = V^T (beta z - d) per (tile, segment)
+  int64_t lr_grid = 0;               // persistent grid of the low-rank kernel
   float* H = nullptr;                // h = M g                (Q x ld)     dense
   float* Wf = nullptr;               // w = beta z - d (FP32)  (Q x ld)     dense fp32
   float* Acc = nullptr;              // M w                    (Q x ld)     dense fp32
@@ -110,9 +111,14 @@ struct ssm_plan_s {
   double* red = nullptr;             // reduction partials
   double* red_out = nullptr;         // finished sums (device)
   double* red_host = nullptr;        // pinned host copy
+  int* dev_err = nullptr;            // device error word (a kernel's bounded wait gave up)
   int red_cap = 0;                   // capacity (rows of 4 doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   void* tc_state = nullptr;          // tensor-core path descriptors (ssm_tc.cu)
+  // optional timing of the dominant kernel of each iteration (ssm_profile_*)
+  bool prof_enabled = false;
+  std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)
+  size_t prof_used = 0;              // pairs recorded since the last read
 };
 
 namespace ssm {
@@ -132,9 +138,13 @@ ssm_status split_bf16(const float* X, int rows, int cols, int64_t ldx,
                       __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, cudaStream_t s);
 
 // low-rank iteration (ssm_lowrank.cu)
-ssm_status lowrank_iteration(ssm_plan_s* pl, int cur, bool check, double* partial,
+// low-rank iteration k -> k+1 with state (z, per-voxel u); `check` forms the residual
+// sums (and reads d^k), `write_d` stores d^{k+1} for the next iteration's test
+ssm_status lowrank_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, double* partial,
                              int* nparts, cudaStream_t s);
 int lowrank_max_partials(const ssm_plan_s* pl);
+int64_t lowrank_grid(const ssm_plan_s* pl);
+int64_t lowrank_partial_floats(const ssm_plan_s* pl, int64_t grid);
 
 // dense iteration and shared kernels (ssm_dense.cu)
 ssm_status sgemm(int M, int N, int K, float alpha, const float* A, int64_t lda,

@@ -8,264 +8,451 @@
 // g_n = V S_n (S_i = sigma_i u_i^T m_n, formed once in FP64) and V^T V = I,
 //     f_n = z_n - d_n/beta + V a_n,
 //     a_i = S_i/(beta + sigma_i^2) - W_i u_i,   u = V^T (beta z - d),
-// none of whose terms is large against the result. u for the next iteration is
-// accumulated while z^{k+1} and d^{k+1} are written, so one pass over the state does
-// the whole iteration:
-//     read  z^k (and its grid neighbours), d^k, a_n
-//     f     = z - d/beta + sum_i V[q][i] a_i
-//     z'    = max(0, (xi z - lambda s (deg z - sum_nbr z) + beta f + d)/(xi + beta))  (Eq. 31)
-//     d'    = d - beta (z' - f)                                                     (step 11)
-//     u'_i += V[q][i] (beta z' - d')
+// none of whose terms is large against the result. Substituting this f into the
+// z-step and the dual step, d cancels from both:
+//     beta f + d = beta (z + V a),   d^{k+1} = beta (z^k + V a^k - z^{k+1}),
+// so the iteration's state is z and the r-vector u per voxel; d is only
+// materialised where the stopping test needs it. One pass over z does the whole
+// iteration:
+//     t     = z + V a                                                (rank-r product)
+//     z'    = max(0, ((xi + beta - lambda s deg) z + lambda s sum_nbr z + beta (V a))
+//                    / (xi + beta))                                  (Eq. 31)
+//     d'    = beta (t - z')                                          (step 11)
+//     u'    = V^T (beta z' - d') = V^T beta (2 z' - t)               (rank-r product)
 // D^T D z = s (deg(n) z_n - sum_{m adjacent} z_m): the free-boundary grid Laplacian,
 // s = 2 for the literal Eq. 8.
 //
-// Mapping: a block owns 32 consecutive voxels (one per lane, coalesced) and QS warps
-// split the Q compartments; the per-voxel sums u' are combined across warps through
-// shared memory in a fixed order (deterministic). Traffic per state element and
-// iteration: read z, d; write z', d' (16 B); neighbour reads hit L1/L2.
+// Mapping (HBM-streaming, TMA-fed, persistent). The work is the flattened list of
+// (voxel tile of 128, compartment) rows; each CTA of a grid sized to the resident
+// capacity takes an equal contiguous share, split into segments at tile boundaries.
+// One producer warp streams a segment's rows in stages of QC compartments with 2D TMA
+// box loads -- z with its x halo, the -+nx (-+nx*ny) neighbour rows, d and the
+// matching rows of V -- into a ring of shared-memory stages guarded by mbarriers.
+// Four consumer warps own one voxel per lane: for every staged compartment they
+// compute f (packed f32x2 FMAs over the rank index), the z-step and the dual step,
+// store z' and d' (coalesced), and fold beta z' - d' into the voxel's u' accumulators
+// kept in registers. At the end of a segment the partial u' goes to a per-(tile,
+// segment) slot; the next iteration sums a tile's slots in segment order (fixed,
+// hence deterministic) when it forms a. HBM traffic per state element and iteration:
+// read z, write z' (8 B); d is read/written only around residual tests; the halo rows
+// are L2 hits. Every mbarrier wait is
+// bounded and reports SSM_ETIMEOUT through the plan's device error word.
+#include <algorithm>
+#include <cstdlib>
+
 #include "ssm_internal.cuh"
+#include "ssm_tma.cuh"
 
 namespace ssm {
 namespace {
 
+constexpr int TV = 128;            // voxels per tile (4 consumer warps x 32 lanes)
+constexpr int NCW = 4;             // consumer warps
+constexpr int NT = 32 * (NCW + 1); // + one producer warp
+constexpr int QC = 8;              // compartments per stage
+constexpr int NB = 3;              // stages in the ring
+constexpr int ZW = TV + 8;         // staged z row: voxels n0-4 .. n0+TV+3
+constexpr int NW = TV + 4;         // staged neighbour row: 4-aligned base .. +TV+4
+
+struct LowrankMaps {
+  CUtensorMap zc;   // z^k, box {ZW, QC}
+  CUtensorMap zn;   // z^k, box {NW, QC}
+  CUtensorMap d;    // d^k, box {TV, QC}
+  CUtensorMap v;    // V (Q x R), box {R, QC}
+};
+
 struct LowrankArgs {
-  const float* __restrict__ Zin;
-  const float* __restrict__ Din;
   float* __restrict__ Zout;
-  float* __restrict__ Dout;
-  const float* __restrict__ V;      // Q x R
+  float* __restrict__ Dout;         // d^{k+1}, written when write_d != 0
   const float* __restrict__ S;      // R x ld
-  const float* __restrict__ Uin;    // R x ld
-  float* __restrict__ Uout;         // R x ld
+  const float* __restrict__ Pin;    // partial u of the previous iteration [tile][seg][R][TV]
+  float* __restrict__ Pout;         // partial u of this iteration
+  int64_t ntiles, T;                // tiles, total rows (ntiles * Q)
+  int maxseg;                       // segment slots per tile
   const float* __restrict__ coefA;  // R
   const float* __restrict__ coefW;  // R
   double* __restrict__ partial;     // 4 doubles per block (check iterations)
+  int* __restrict__ err;            // device error word (SSM_ETIMEOUT on a failed wait)
   Grid g;
-  int Q, qchunk;
+  int Q;
+  int write_d;
   float beta, inv_beta, xi, lam_s, inv_xb;
 };
 
-template <int R>
-struct MaxThreads {
-  static constexpr int value = R <= 24 ? 512 : (R <= 48 ? 256 : 128);
+// shared-memory layout (bytes), every TMA destination 128-byte aligned
+struct Layout {
+  int zc, zn, dd, vv, stage;   // offsets inside one stage, stage size
+  int bars, total;             // mbarriers after the stages, total bytes
+  __host__ __device__ Layout(int R, int NR) {
+    auto al = [](int b) { return (b + 127) / 128 * 128; };
+    zc = 0;
+    zn = al(zc + QC * ZW * 4);
+    dd = al(zn + NR * QC * NW * 4);
+    vv = al(dd + QC * TV * 4);
+    stage = al(vv + QC * R * 4);
+    bars = NB * stage;
+    total = bars + 2 * NB * 8;
+  }
 };
 
-template <int R, bool CHECK>
-__global__ void __launch_bounds__(MaxThreads<R>::value)
-    lowrank_iter_kernel(LowrankArgs a) {
-  extern __shared__ float smem[];
-  const int lane = threadIdx.x;
-  const int wy = threadIdx.y;
-  const int QS = blockDim.y;
-  const int64_t ld = a.g.ld;
-  const int64_t tile0 = (int64_t)blockIdx.x * 32;
-  const int64_t n = tile0 + lane;
-  const bool valid = n < a.g.N;
+__host__ __device__ __forceinline__ int64_t floor4(int64_t v) {
+  return v >= 0 ? (v & ~(int64_t)3) : -(((-v) + 3) & ~(int64_t)3);
+}
 
-  // a_i for the tile's 32 voxels, computed once per block
-  for (int idx = wy * 32 + lane; idx < R * 32; idx += 32 * QS) {
-    const int i = idx >> 5;
-    const int64_t nn = tile0 + (idx & 31);
-    float v = 0.f;
-    if (nn < a.g.N)
-      v = __ldg(a.S + i * ld + nn) * __ldg(a.coefA + i) - __ldg(a.coefW + i) * __ldg(a.Uin + i * ld + nn);
-    smem[idx] = v;
+// contiguous share [lo, hi) of the flattened rows for CTA j of G
+__host__ __device__ __forceinline__ int64_t share_lo(int64_t T, int64_t j, int64_t G) {
+  return (T * j) / G;
+}
+// the first CTA whose share contains flattened row r
+__host__ __device__ __forceinline__ int64_t owner_of(int64_t r, int64_t T, int64_t G) {
+  return ((r + 1) * G + T - 1) / T - 1;
+}
+
+template <int R, bool CHECK>
+__global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant__ LowrankMaps maps,
+                                                          const LowrankArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // TMA destinations must be 128-byte aligned: align the dynamic window explicitly
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int64_t ld = a.g.ld;
+  const int64_t N = a.g.N;
+  const int Q = a.Q;
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const int NR = (ny > 1 ? 2 : 0) + (nz > 1 ? 2 : 0);
+  const Layout L(R, NR);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint64_t* empty = full + NB;
+  // neighbour row offsets in flat index: -nx, +nx, -nx*ny, +nx*ny (present axes only)
+  int64_t off[4] = {0, 0, 0, 0};
+  {
+    int k = 0;
+    if (ny > 1) { off[k++] = -(int64_t)nx; off[k++] = nx; }
+    if (nz > 1) { off[k++] = -(int64_t)nx * ny; off[k++] = (int64_t)nx * ny; }
+  }
+  const int64_t G = gridDim.x;
+  const int64_t lo = share_lo(a.T, blockIdx.x, G);
+  const int64_t hi = share_lo(a.T, blockIdx.x + 1, G);
+  // d^k is staged only on residual-test iterations (it enters f, not z' or u')
+  const unsigned stage_bytes = (unsigned)(QC * ZW * 4 + NR * QC * NW * 4 +
+                                          (CHECK ? QC * TV * 4 : 0) + QC * R * 4);
+
+  if (tid == 0) {
+    for (int b = 0; b < NB; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], NCW);
+    }
+    mbar_fence_init();
   }
   __syncthreads();
-  float av[R], acc[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    av[i] = smem[i * 32 + lane];
-    acc[i] = 0.f;
-  }
-
-  // grid coordinates and free-boundary neighbour flags
-  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const int64_t sy = nx, sz = (int64_t)nx * ny;
-  int x = 0, y = 0, zc = 0;
-  if (valid) {
-    x = (int)(n % nx);
-    const int64_t t = n / nx;
-    y = (int)(t % ny);
-    zc = (int)(t / ny);
-  }
-  const bool hxm = x > 0, hxp = x < nx - 1;
-  const bool hym = y > 0, hyp = y < ny - 1;
-  const bool hzm = zc > 0, hzp = zc < nz - 1;
-  const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
-
-  const int q0 = wy * a.qchunk;
-  const int q1 = min(a.Q, q0 + a.qchunk);
+  bool failed = false;
   float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  if (valid) {
-#pragma unroll 2
-    for (int q = q0; q < q1; ++q) {
-      const int64_t o = (int64_t)q * ld + n;
-      const float z = __ldg(a.Zin + o);
-      const float d = __ldg(a.Din + o);
-      float nb = 0.f;
-      if (hxm) nb += __ldg(a.Zin + o - 1);
-      if (hxp) nb += __ldg(a.Zin + o + 1);
-      if (hym) nb += __ldg(a.Zin + o - sy);
-      if (hyp) nb += __ldg(a.Zin + o + sy);
-      if (hzm) nb += __ldg(a.Zin + o - sz);
-      if (hzp) nb += __ldg(a.Zin + o + sz);
-      const float4* v4 = reinterpret_cast<const float4*>(a.V + (int64_t)q * R);
-      float vr[R];
-#pragma unroll
-      for (int i = 0; i < R / 4; ++i) {
-        const float4 t = __ldg(v4 + i);
-        vr[4 * i] = t.x;
-        vr[4 * i + 1] = t.y;
-        vr[4 * i + 2] = t.z;
-        vr[4 * i + 3] = t.w;
-      }
-      float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-      for (int i = 0; i < R; i += 2) {
-        f0 = fmaf(vr[i], av[i], f0);
-        f1 = fmaf(vr[i + 1], av[i + 1], f1);
-      }
-      const float f = (z - d * a.inv_beta) + (f0 + f1);
-      const float lap = deg * z - nb;
-      const float zn = fmaxf(0.f, (a.xi * z - a.lam_s * lap + a.beta * f + d) * a.inv_xb);
-      const float dn = d - a.beta * (zn - f);
-      const float w = a.beta * zn - dn;
-#pragma unroll
-      for (int i = 0; i < R; ++i) acc[i] = fmaf(vr[i], w, acc[i]);
-      a.Zout[o] = zn;
-      a.Dout[o] = dn;
-      if (CHECK) {
-        const float e = zn - f, c = zn - z;
-        s1 = fmaf(e, e, s1);
-        s2 = fmaf(c, c, s2);
-        s3 = fmaf(zn, zn, s3);
+  const float c2 = a.lam_s * a.inv_xb;     // weight of the neighbour sum
+  const float c3 = a.beta * a.inv_xb;      // weight of V a
+
+  if (warp == NCW) {
+    // ------------------------------- producer warp: one elected lane issues TMA
+    if (lane == 0) {
+      tma_prefetch_map(&maps.zc);
+      tma_prefetch_map(&maps.d);
+      int c = 0;   // running stage counter over all segments
+      for (int64_t r = lo; r < hi && !failed;) {
+        const int64_t tile = r / Q;
+        const int64_t n0 = tile * TV;
+        const int q0 = (int)(r - tile * Q);
+        const int qend = (int)(min(hi, (tile + 1) * Q) - tile * Q);
+        for (int q = q0; q < qend; q += QC, ++c) {
+          const int b = c % NB;
+          const int k = c / NB;
+          if (c >= NB && !mbar_wait(&empty[b], (k - 1) & 1)) {
+            failed = true;
+            break;
+          }
+          unsigned char* st = smem + b * L.stage;
+          mbar_arrive_expect_tx(&full[b], stage_bytes);
+          tma_load_2d(st + L.zc, &maps.zc, (int)(n0 - 4), q, &full[b]);
+          for (int j = 0; j < NR; ++j)
+            tma_load_2d(st + L.zn + j * QC * NW * 4, &maps.zn, (int)floor4(n0 + off[j]), q,
+                        &full[b]);
+          if (CHECK) tma_load_2d(st + L.dd, &maps.d, (int)n0, q, &full[b]);
+          tma_load_2d(st + L.vv, &maps.v, 0, q, &full[b]);
+        }
+        r = tile * Q + qend;
       }
     }
-  }
-  __syncthreads();
-  // combine the QS partial projections per voxel (fixed order)
+  } else {
+    // ------------------------------- consumer warps: one voxel per lane
+    const int v = warp * 32 + lane;
+    int c = 0;
+    for (int64_t r = lo; r < hi;) {
+      const int64_t tile = r / Q;
+      const int64_t n0 = tile * TV;
+      const int q0 = (int)(r - tile * Q);
+      const int qend = (int)(min(hi, (tile + 1) * Q) - tile * Q);
+      const int64_t n = n0 + v;
+      const bool valid = n < N;
+      int x = 0, y = 0, zc = 0;
+      if (valid) {
+        x = (int)(n % nx);
+        const int64_t t = n / nx;
+        y = (int)(t % ny);
+        zc = (int)(t / ny);
+      }
+      const bool hxm = valid && x > 0, hxp = valid && x < nx - 1;
+      const bool hym = valid && y > 0, hyp = valid && y < ny - 1;
+      const bool hzm = valid && zc > 0, hzp = valid && zc < nz - 1;
+      const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
+      const float e1 = (a.xi + a.beta - a.lam_s * deg) * a.inv_xb;   // weight of z
+      int nidx[4];
+      bool nok[4];
+      {
+        const bool flags[4] = {ny > 1 ? hym : hzm, ny > 1 ? hyp : hzp, hzm, hzp};
 #pragma unroll
-  for (int i = 0; i < R; ++i) smem[(wy * R + i) * 32 + lane] = acc[i];
-  __syncthreads();
-  for (int idx = wy * 32 + lane; idx < R * 32; idx += 32 * QS) {
-    const int i = idx >> 5, l = idx & 31;
-    float sum = 0.f;
-    for (int y2 = 0; y2 < QS; ++y2) sum += smem[(y2 * R + i) * 32 + l];
-    const int64_t nn = tile0 + l;
-    if (nn < a.g.N) a.Uout[i * ld + nn] = sum;
+        for (int j = 0; j < 4; ++j) {
+          nidx[j] = j < NR ? (int)(n + off[j] - floor4(n0 + off[j])) : 0;
+          nok[j] = j < NR && flags[j];
+        }
+      }
+      // a_i = S_i/(beta + sigma_i^2) - W_i u_i, u_i summed over the tile's segment
+      // slots of the previous iteration in segment order
+      const int64_t j0 = owner_of(tile * Q, a.T, G);
+      const int nseg = (int)(owner_of(tile * Q + Q - 1, a.T, G) - j0 + 1);
+      const int sidx = (int)(blockIdx.x - j0);
+      float2 av[R / 2];
+#pragma unroll
+      for (int i = 0; i < R / 2; ++i) {
+        float a0 = 0.f, a1 = 0.f;
+        if (valid) {
+          float u0 = 0.f, u1 = 0.f;
+          const float* pt = a.Pin + (tile * a.maxseg) * (int64_t)(R * TV);
+          for (int sg = 0; sg < nseg; ++sg) {
+            u0 += pt[(sg * R + 2 * i) * TV + v];
+            u1 += pt[(sg * R + 2 * i + 1) * TV + v];
+          }
+          a0 = __ldg(a.S + (2 * i) * ld + n) * __ldg(a.coefA + 2 * i) - __ldg(a.coefW + 2 * i) * u0;
+          a1 = __ldg(a.S + (2 * i + 1) * ld + n) * __ldg(a.coefA + 2 * i + 1) -
+               __ldg(a.coefW + 2 * i + 1) * u1;
+        }
+        av[i] = make_float2(a0, a1);
+      }
+      float2 uacc[R / 2];
+#pragma unroll
+      for (int i = 0; i < R / 2; ++i) uacc[i] = make_float2(0.f, 0.f);
+      for (int qc0 = q0; qc0 < qend; qc0 += QC, ++c) {
+        const int b = c % NB;
+        const int k = c / NB;
+        if (!failed && !mbar_wait(&full[b], k & 1)) failed = true;
+        const unsigned char* st = smem + b * L.stage;
+        const float* zcr = reinterpret_cast<const float*>(st + L.zc);
+        const float* znr = reinterpret_cast<const float*>(st + L.zn);
+        const float* ddr = reinterpret_cast<const float*>(st + L.dd);
+        const float* vvr = reinterpret_cast<const float*>(st + L.vv);
+        const int qn = min(QC, qend - qc0);
+        if (!failed && valid) {
+#pragma unroll 2
+          for (int row = 0; row < qn; ++row) {
+            const float z = zcr[row * ZW + 4 + v];
+            float nb = 0.f;
+            if (hxm) nb += zcr[row * ZW + 3 + v];
+            if (hxp) nb += zcr[row * ZW + 5 + v];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (nok[j]) nb += znr[(j * QC + row) * NW + nidx[j]];
+            const float4* v4 = reinterpret_cast<const float4*>(vvr + row * R);
+            float2 p0 = make_float2(0.f, 0.f), p1 = make_float2(0.f, 0.f);
+            float4 vr[R / 4];
+#pragma unroll
+            for (int i = 0; i < R / 4; ++i) {
+              vr[i] = v4[i];
+              p0 = __ffma2_rn(make_float2(vr[i].x, vr[i].y), av[2 * i], p0);
+              p1 = __ffma2_rn(make_float2(vr[i].z, vr[i].w), av[2 * i + 1], p1);
+            }
+            const float va = (p0.x + p0.y) + (p1.x + p1.y);     // (V a)_q
+            const float zn = fmaxf(0.f, fmaf(e1, z, fmaf(c2, nb, c3 * va)));
+            const float t = z + va;
+            const float w = a.beta * (2.f * zn - t);            // beta z' - d'
+            const float2 ww = make_float2(w, w);
+#pragma unroll
+            for (int i = 0; i < R / 4; ++i) {
+              uacc[2 * i] = __ffma2_rn(make_float2(vr[i].x, vr[i].y), ww, uacc[2 * i]);
+              uacc[2 * i + 1] = __ffma2_rn(make_float2(vr[i].z, vr[i].w), ww, uacc[2 * i + 1]);
+            }
+            const int64_t o = (int64_t)(qc0 + row) * ld + n;
+            a.Zout[o] = zn;
+            if (a.write_d) a.Dout[o] = a.beta * (t - zn);
+            if (CHECK) {
+              const float f = t - ddr[row * TV + v] * a.inv_beta;   // f^{k+1}
+              const float e = zn - f, ch = zn - z;
+              s1 = fmaf(e, e, s1);
+              s2 = fmaf(ch, ch, s2);
+              s3 = fmaf(zn, zn, s3);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+      }
+      // this segment's partial u' (zero for voxels past the grid)
+      float* po = a.Pout + ((tile * a.maxseg + sidx) * (int64_t)R) * TV;
+#pragma unroll
+      for (int i = 0; i < R / 2; ++i) {
+        po[(2 * i) * TV + v] = valid ? uacc[i].x : 0.f;
+        po[(2 * i + 1) * TV + v] = valid ? uacc[i].y : 0.f;
+      }
+      r = tile * Q + qend;
+    }
   }
+  if (failed) atomicExch(a.err, (int)SSM_ETIMEOUT);
   if (CHECK) {
     double d1 = s1, d2 = s2, d3 = s3;
-    for (int off = 16; off > 0; off >>= 1) {
-      d1 += __shfl_xor_sync(0xffffffffu, d1, off);
-      d2 += __shfl_xor_sync(0xffffffffu, d2, off);
-      d3 += __shfl_xor_sync(0xffffffffu, d3, off);
+    for (int o = 16; o > 0; o >>= 1) {
+      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      d3 += __shfl_xor_sync(0xffffffffu, d3, o);
     }
-    __syncthreads();
-    double* dsm = reinterpret_cast<double*>(smem);
+    __shared__ double red[NT / 32][3];
     if (lane == 0) {
-      dsm[wy * 3 + 0] = d1;
-      dsm[wy * 3 + 1] = d2;
-      dsm[wy * 3 + 2] = d3;
+      red[warp][0] = d1;
+      red[warp][1] = d2;
+      red[warp][2] = d3;
     }
     __syncthreads();
-    if (wy == 0 && lane < 3) {
+    if (tid < 3) {
       double t = 0.0;
-      for (int y2 = 0; y2 < QS; ++y2) t += dsm[y2 * 3 + lane];
-      a.partial[(int64_t)blockIdx.x * 4 + lane] = t;
+      for (int w = 0; w < NT / 32; ++w) t += red[w][tid];
+      a.partial[(int64_t)blockIdx.x * 4 + tid] = t;
     }
   }
-}
-
-template <int R>
-int qs_max() {
-  return MaxThreads<R>::value / 32;
-}
-
-template <int R>
-ssm_status launch_r(const LowrankArgs& args, bool check, int nblocks, int qs, cudaStream_t s) {
-  const size_t shm = sizeof(float) * (size_t)R * 32 * qs;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(lowrank_iter_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         96 * 1024);
-    cudaFuncSetAttribute(lowrank_iter_kernel<R, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    configured = true;
-  }
-  dim3 block(32, qs), grid(nblocks);
-  if (check)
-    lowrank_iter_kernel<R, true><<<grid, block, shm, s>>>(args);
-  else
-    lowrank_iter_kernel<R, false><<<grid, block, shm, s>>>(args);
-  SSM_LAUNCHED();
-  return SSM_OK;
-}
-
-// q-split: enough warps to fill the GPU (about 48 resident warps on each of the SMs),
-// at least 16 compartments per warp, within the register budget of the rank.
-int choose_qs(int64_t ntiles, int Q, int qsmax, int nsm) {
-  const int64_t want = (int64_t)nsm * 48;
-  int qs = 1;
-  while (qs < qsmax && ntiles * qs < want && Q / (qs * 2) >= 16) qs *= 2;
-  return qs;
 }
 
 int g_nsm = 0;
 
+template <int R>
+size_t smem_for(int nr) { return (size_t)Layout(R, nr).total + 128; }
+
+template <int R>
+ssm_status launch_r(const LowrankMaps& maps, const LowrankArgs& args, bool check, int64_t grid,
+                    cudaStream_t s) {
+  const size_t shm = smem_for<R>((args.g.ny > 1 ? 2 : 0) + (args.g.nz > 1 ? 2 : 0));
+  if (check)
+    lowrank_iter_kernel<R, true><<<(unsigned)grid, NT, shm, s>>>(maps, args);
+  else
+    lowrank_iter_kernel<R, false><<<(unsigned)grid, NT, shm, s>>>(maps, args);
+  SSM_LAUNCHED();
+  return SSM_OK;
+}
+
+// resident CTAs per SM for rank R (registers and shared memory), set up once per R
+template <int R>
+int blocks_per_sm(int nr) {
+  static int cached[5] = {0, 0, 0, 0, 0};
+  if (cached[nr] == 0) {
+    const size_t shm = smem_for<R>(nr);
+    cudaFuncSetAttribute(lowrank_iter_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)shm);
+    cudaFuncSetAttribute(lowrank_iter_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)shm);
+    int b1 = 0, b2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, lowrank_iter_kernel<R, true>, NT, shm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, lowrank_iter_kernel<R, false>, NT, shm);
+    cached[nr] = std::max(1, std::min(b1, b2));
+  }
+  return cached[nr];
+}
+
+// tensor maps of the current ping-pong state (encoding is a ~1 us host computation)
+ssm_status build_maps(const ssm_plan_s* pl, int cur, LowrankMaps* m) {
+  const uint64_t N = (uint64_t)pl->g.N, Q = (uint64_t)pl->Q, ld = (uint64_t)pl->g.ld;
+  SSM_CUDA(encode_2d(&m->zc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pl->Z[cur], N, Q, ld, ZW, QC));
+  SSM_CUDA(encode_2d(&m->zn, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pl->Z[cur], N, Q, ld, NW, QC));
+  SSM_CUDA(encode_2d(&m->d, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pl->Dl[cur], N, Q, ld, TV, QC));
+  SSM_CUDA(encode_2d(&m->v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pl->V32, (uint64_t)pl->R, Q,
+                     (uint64_t)pl->R, (unsigned)pl->R, QC));
+  return SSM_OK;
+}
+
+
+int bpsm_for(int R, int nr) {
+  switch (R) {
+#define SSM_R(RR) \
+  case RR:        \
+    return blocks_per_sm<RR>(nr);
+    SSM_R(4) SSM_R(8) SSM_R(12) SSM_R(16) SSM_R(20) SSM_R(24) SSM_R(28) SSM_R(32)
+    SSM_R(40) SSM_R(48) SSM_R(56) SSM_R(64)
+#undef SSM_R
+    default:
+      return 1;
+  }
+}
+
 }  // namespace
 
-int lowrank_max_partials(const ssm_plan_s* pl) { return (int)((pl->g.N + 31) / 32); }
-
-ssm_status lowrank_iteration(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
-                             cudaStream_t s) {
+// persistent grid: every resident slot, but at least two stages of rows per CTA
+int64_t lowrank_grid(const ssm_plan_s* pl) {
   if (g_nsm == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
     if (g_nsm <= 0) g_nsm = 148;
   }
+  const int nr = (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 ? 2 : 0);
+  const int64_t ntiles = (pl->g.N + TV - 1) / TV;
+  const int64_t T = ntiles * pl->Q;
+  int64_t grid = (int64_t)g_nsm * bpsm_for(pl->R, nr);
+  if (const char* env = getenv("SSM_LOWRANK_GRID")) {   // launch-shape override for sweeps
+    const long v = atol(env);
+    if (v >= 1 && v <= 65536) grid = v;
+  }
+  return std::max<int64_t>(1, std::min(grid, (T + 2 * QC - 1) / (2 * QC)));
+}
+
+// segment slots per tile: a tile's rows are shared by at most ceil(G/ntiles) + 1 CTAs
+int lowrank_maxseg(const ssm_plan_s* pl, int64_t grid) {
+  const int64_t ntiles = (pl->g.N + TV - 1) / TV;
+  return (int)((grid + ntiles - 1) / ntiles + 1);
+}
+
+int64_t lowrank_partial_floats(const ssm_plan_s* pl, int64_t grid) {
+  const int64_t ntiles = (pl->g.N + TV - 1) / TV;
+  return ntiles * lowrank_maxseg(pl, grid) * (int64_t)pl->R * TV;
+}
+
+int lowrank_max_partials(const ssm_plan_s* pl) { return (int)lowrank_grid(pl); }
+
+ssm_status lowrank_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, double* partial,
+                             int* nparts, cudaStream_t s) {
+  LowrankMaps maps;
+  SSM_TRY(build_maps(pl, cur, &maps));
+  const int64_t grid = pl->lr_grid;
   LowrankArgs a;
-  a.Zin = pl->Z[cur];
-  a.Din = pl->Dl[cur];
   a.Zout = pl->Z[cur ^ 1];
   a.Dout = pl->Dl[cur ^ 1];
-  a.V = pl->V32;
   a.S = pl->S;
-  a.Uin = pl->U[cur];
-  a.Uout = pl->U[cur ^ 1];
+  a.Pin = pl->U[cur];
+  a.Pout = pl->U[cur ^ 1];
+  a.ntiles = (pl->g.N + TV - 1) / TV;
+  a.T = a.ntiles * pl->Q;
+  a.maxseg = lowrank_maxseg(pl, grid);
   a.coefA = pl->coefA;
   a.coefW = pl->coefW;
   a.partial = partial;
+  a.err = pl->dev_err;
   a.g = pl->g;
   a.Q = pl->Q;
+  a.write_d = write_d ? 1 : 0;
   a.beta = (float)pl->p.beta;
   a.inv_beta = (float)(1.0 / pl->p.beta);
   a.xi = (float)pl->xi;
   a.lam_s = (float)pl->lam_s;
   a.inv_xb = (float)(1.0 / (pl->xi + pl->p.beta));
-  const int ntiles = lowrank_max_partials(pl);
-  *nparts = ntiles;
-  int qsmax = 1;
-  switch (pl->R) {
-#define SSM_QS(RR) \
-  case RR:         \
-    qsmax = qs_max<RR>(); \
-    break;
-    SSM_QS(4) SSM_QS(8) SSM_QS(12) SSM_QS(16) SSM_QS(20) SSM_QS(24) SSM_QS(28) SSM_QS(32)
-    SSM_QS(40) SSM_QS(48) SSM_QS(56) SSM_QS(64)
-#undef SSM_QS
-    default:
-      set_error("low-rank kernel: unsupported padded rank");
-      return SSM_EUNSUPPORTED;
-  }
-  const int qs = choose_qs(ntiles, pl->Q, qsmax, g_nsm);
-  a.qchunk = (pl->Q + qs - 1) / qs;
+  *nparts = (int)grid;
   switch (pl->R) {
 #define SSM_R(RR) \
   case RR:        \
-    return launch_r<RR>(a, check, ntiles, qs, s);
+    return launch_r<RR>(maps, a, check, grid, s);
     SSM_R(4) SSM_R(8) SSM_R(12) SSM_R(16) SSM_R(20) SSM_R(24) SSM_R(28) SSM_R(32)
     SSM_R(40) SSM_R(48) SSM_R(56) SSM_R(64)
 #undef SSM_R

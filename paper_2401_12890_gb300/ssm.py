@@ -17,7 +17,8 @@ import re
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libssm.so")
+# SSM_LIBRARY selects another build of the library (e.g. an instrumented one)
+LIB_PATH = os.environ.get("SSM_LIBRARY", os.path.join(HERE, "libssm.so"))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ssm.h")
 
 SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENAN, SSM_ETIMEOUT, SSM_EUNSUPPORTED, \
@@ -86,12 +87,15 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_objective.argtypes = [vp, fp, i64, fp, i64, ctypes.c_int, dp, vp]
     lib.ssm_plan_factors.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     lib.ssm_destroy.argtypes = [vp]
+    lib.ssm_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.ssm_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_status_string.argtypes = [ctypes.c_int]
     lib.ssm_status_string.restype = ctypes.c_char_p
     lib.ssm_last_error.restype = ctypes.c_char_p
     lib.ssm_launch_count.restype = ctypes.c_int64
     for name in ("ssm_default_params", "ssm_plan", "ssm_solve", "ssm_solve_host",
-                 "ssm_objective", "ssm_plan_factors", "ssm_destroy"):
+                 "ssm_objective", "ssm_plan_factors", "ssm_destroy", "ssm_profile_enable",
+                 "ssm_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -201,6 +205,21 @@ class Plan:
             if st != SSM_OK:
                 raise SsmError(st, "ssm_plan_factors")
         return sig, vr, r.value
+
+    def profile(self, enable=True):
+        """Time the dominant kernel of every iteration with CUDA events."""
+        st = load_library().ssm_profile_enable(self._h, int(bool(enable)))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_profile_enable")
+
+    def profile_read(self):
+        """(summed device ms, launches) of the dominant kernel since the last read."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        st = load_library().ssm_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_profile_read")
+        return ms.value, n.value
 
     def close(self):
         if self._h:
