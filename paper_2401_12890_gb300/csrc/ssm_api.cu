@@ -299,9 +299,12 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
       SSM_TRY(dalloc(&pl->Acc, QN, s));
       maxparts = dense_max_partials(pl);
     } else {
+      // w for the tensor-core operand: voxel-major rows of Qp compartments
+      const size_t WN = (size_t)pl->g.ld * pl->Qp;
+      SSM_TRY(dalloc(&pl->Acc, QN, s));
       for (int i = 0; i < 2; ++i) {
-        SSM_TRY(dalloc(&pl->Whi[i], QN, s));
-        SSM_TRY(dalloc(&pl->Wlo[i], QN, s));
+        SSM_TRY(dalloc(&pl->Whi[i], WN, s));
+        SSM_TRY(dalloc(&pl->Wlo[i], WN, s));
       }
       SSM_TRY(tc_prepare(pl, s));
       maxparts = std::max(tc_max_partials(pl), dense_max_partials(pl));
@@ -383,8 +386,10 @@ ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, bool check_next, i
     SSM_TRY(prof_mark(pl, false, s));
     return dense_update(pl, cur, pl->Acc, check, true, false, pl->red, nparts, s);
   }
-  SSM_TRY(tc_iteration(pl, cur, check, pl->red, nparts, s));
-  return prof_mark(pl, false, s);
+  // the dominant kernel of the tensor-core form is the product M w
+  SSM_TRY(tc_gemm(pl, cur, s));
+  SSM_TRY(prof_mark(pl, false, s));
+  return tc_update(pl, cur, check, pl->red, nparts, s);
 }
 
 ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int64_t ldf,
@@ -407,8 +412,9 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
                   s));
     if (pl->Wf) SSM_CUDA(cudaMemsetAsync(pl->Wf, 0, sizeof(float) * QN, s));
     if (pl->Whi[0]) {
-      SSM_CUDA(cudaMemsetAsync(pl->Whi[0], 0, sizeof(__nv_bfloat16) * QN, s));
-      SSM_CUDA(cudaMemsetAsync(pl->Wlo[0], 0, sizeof(__nv_bfloat16) * QN, s));
+      const size_t WN = (size_t)pl->g.ld * pl->Qp;
+      SSM_CUDA(cudaMemsetAsync(pl->Whi[0], 0, sizeof(__nv_bfloat16) * WN, s));
+      SSM_CUDA(cudaMemsetAsync(pl->Wlo[0], 0, sizeof(__nv_bfloat16) * WN, s));
     }
   }
   // step 2: z = d = 0

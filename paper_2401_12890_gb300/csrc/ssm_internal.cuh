@@ -163,6 +163,9 @@ ssm_status objective_terms(const ssm_plan_s* pl, const float* Res, int P, const 
 ssm_status tc_prepare(ssm_plan_s* pl, cudaStream_t s);
 ssm_status tc_iteration(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
                         cudaStream_t s);
+ssm_status tc_gemm(ssm_plan_s* pl, int cur, cudaStream_t s);
+ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
+                     cudaStream_t s);
 void tc_release(ssm_plan_s* pl);
 int tc_max_partials(const ssm_plan_s* pl);
 

@@ -1,19 +1,580 @@
-// Tensor-core (tcgen05) BF16 hi/lo form of the full-rank iteration: not built yet.
+// Full-rank (Eq. 26) LADMM iteration on the tcgen05 tensor cores, BF16 split products.
+//
+// The f-step of Eq. 26 is f = h + M w with M = (K^T K + beta I)^{-1} (Q x Q, formed
+// once in FP64), h = M g (once per solve) and w = beta z - d. An iteration is two
+// kernels:
+//   tc_gemm_kernel    acc = M w on the tensor cores (tcgen05.mma, TMA-fed, FP32 in TMEM)
+//   tc_update_kernel  the bandwidth-bound rest, TMA-staged:
+//       f  = h + acc
+//       z' = max(0, (xi z - lambda s (deg z - sum_nbr z) + beta f + d) / (xi + beta))  (Eq. 31)
+//       d' = d - beta (z' - f)                                                      (step 11)
+//       w' = beta z' - d'   -> stored as the BF16 pair (hi, lo) for the next product
+//
+// Precision ("BF16x3"): w and M are each split into BF16 hi + lo parts
+// (x_hi = bf16(x), x_lo = bf16(x - x_hi)), and M w is accumulated in FP32 in tensor
+// memory as M_hi w_hi + M_hi w_lo + M_lo w_hi (the lo*lo term, ~2^-16 relative, is
+// dropped). z, d, h and f stay FP32.
+//
+// GEMM operands: w is kept voxel-major (row n holds its Q compartments, stride Qp), so
+// both MMA operands are K-major: A = w tile (128 voxels x 64 compartments), B = M tile
+// (256 output compartments x 64), each a 128-byte-swizzled TMA box. The accumulator
+// (128 voxels x 256 compartments, FP32) lives in TMEM, with TMEM lanes = voxels, so
+// the epilogue's stores of acc into the map-major Q x N array coalesce.
+//
+// GEMM schedule: one persistent CTA per SM walks (voxel tile, compartment tile) pairs,
+// voxel-tile major so concurrently running CTAs share w tiles in L2. Warp 0 issues TMA
+// loads into a smem ring; one thread of warp 1 issues the tcgen05.mma chain (3 MMAs
+// per K = 16 step) and commits stage releases and accumulator completions to
+// mbarriers; warps 2-5 drain the accumulator (tcgen05.ld) to global memory. Two
+// 256-column accumulators alternate so draining one tile overlaps the next tile's
+// MMAs. Every mbarrier wait is bounded.
+#include <algorithm>
+
 #include "ssm_internal.cuh"
+#include "ssm_tma.cuh"
 
 namespace ssm {
+namespace {
+
+constexpr int BM = 128;                         // voxels per tile (MMA M, TMEM lanes)
+constexpr int BN = 256;                         // compartments per tile (MMA N)
+constexpr int BK = 64;                          // K per stage: one 128-byte swizzle atom
+constexpr int UK = 16;                          // K per tcgen05.mma (kind::f16)
+constexpr int NS = 2;                           // smem stages
+constexpr int NTHR = 192;                       // TMA warp, MMA warp, 4 epilogue warps
+constexpr uint32_t TMEM_COLS = 512;             // two BN-column FP32 accumulators
+constexpr int A_BYTES = BM * BK * 2;            // 16 KB
+constexpr int B_BYTES = BN * BK * 2;            // 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int SMEM_BYTES = NS * STAGE_BYTES + 1024 + 256;
+
+// kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct TcMaps {
+  CUtensorMap a_hi, a_lo;   // w (voxel-major), box {BK, BM}
+  CUtensorMap b_hi, b_lo;   // M, box {BK, BN}
+};
+
+struct TcArgs {
+  float* __restrict__ Acc;           // M w, map-major Q x N (row stride ld)
+  int* __restrict__ err;
+  Grid g;
+  int Q, ntv, ntq;
+};
+
+// shared-memory matrix descriptor, K-major operand in the 128-byte swizzle layout:
+// start address >> 4 (bits 0-13), leading byte offset 16 B (unused for this layout),
+// stride byte offset 1024 B = 8 rows x 128 B (bits 32-45), version 1 (bit 46),
+// base offset 0, swizzle mode 2 = 128 B (bits 61-63)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
+  return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
+}
+
+__global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant__ TcMaps maps,
+                                                          const TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * STAGE_BYTES);
+  uint64_t* empty = full + NS;
+  uint64_t* tfull = empty + NS;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int ntiles = a.ntv * a.ntq;
+  const int nk = (a.Q + BK - 1) / BK;
+  bool failed = false;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      tma_prefetch_map(&maps.a_hi);
+      tma_prefetch_map(&maps.b_hi);
+      int c = 0;
+      for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+        const int vt = t / a.ntq, qt = t % a.ntq;
+        for (int kc = 0; kc < nk; ++kc, ++c) {
+          const int s = c % NS, r = c / NS;
+          if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1)) {
+            failed = true;
+            break;
+          }
+          unsigned char* st = smem + s * STAGE_BYTES;
+          mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(st, &maps.a_hi, kc * BK, vt * BM, &full[s]);
+          tma_load_2d(st + A_BYTES, &maps.a_lo, kc * BK, vt * BM, &full[s]);
+          tma_load_2d(st + 2 * A_BYTES, &maps.b_hi, kc * BK, qt * BN, &full[s]);
+          tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.b_lo, kc * BK, qt * BN, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int c = 0, it = 0;
+      for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x, ++it) {
+        const int acc = it & 1, ra = it >> 1;
+        if (ra > 0 && !mbar_wait(&tempty[acc], (ra - 1) & 1)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        for (int kc = 0; kc < nk; ++kc, ++c) {
+          const int s = c % NS, r = c / NS;
+          if (!mbar_wait(&full[s], r & 1)) {
+            failed = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / UK; ++kk) {
+            const uint64_t ahi = smem_desc(base + kk * 32);
+            const uint64_t alo = smem_desc(base + A_BYTES + kk * 32);
+            const uint64_t bhi = smem_desc(base + 2 * A_BYTES + kk * 32);
+            const uint64_t blo = smem_desc(base + 2 * A_BYTES + B_BYTES + kk * 32);
+            mma_bf16(d_tmem, ahi, bhi, (kc | kk) ? 1u : 0u);
+            mma_bf16(d_tmem, alo, bhi, 1u);
+            mma_bf16(d_tmem, ahi, blo, 1u);
+          }
+          mma_commit(&empty[s]);      // the stage is free once these MMAs complete
+        }
+        mma_commit(&tfull[acc]);      // the accumulator is complete
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ accumulator drain
+    const int quarter = warp & 3;                  // TMEM lanes 32*quarter .. +31
+    const int row = quarter * 32 + lane;           // voxel within the tile
+    const int64_t ld = a.g.ld, N = a.g.N;
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int acc = it & 1, ra = it >> 1;
+      if (!failed && !mbar_wait(&tfull[acc], ra & 1)) failed = true;
+      tc_fence_after();
+      const int vt = t / a.ntq, qt = t % a.ntq;
+      const int64_t n = (int64_t)vt * BM + row;
+      const bool valid = n < N && !failed;
+      for (int cc = 0; cc < BN / 32; ++cc) {
+        const int q0 = qt * BN + cc * 32;
+        if (q0 >= a.Q) break;                       // uniform across the warp
+        float v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN + cc * 32),
+                  v);
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (q0 + j < a.Q) a.Acc[(int64_t)(q0 + j) * ld + n] = v[j];
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+  }
+  if (failed) atomicExch(a.err, (int)SSM_ETIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// tc_update_kernel: the z-step, dual step and next-w split, TMA-staged (HBM-bound)
+// ------------------------------------------------------------------------------------
+// A CTA owns a voxel tile of 128 and a contiguous share of the (tile, 8-compartment
+// chunk) list; one producer warp streams z (x halo), its -+nx (-+nx*ny) neighbour
+// rows, d, h and acc for each chunk with 2D TMA boxes into a 2-stage mbarrier ring;
+// four consumer warps own a voxel per lane, compute the 8 compartments of the chunk,
+// store z' and d' (coalesced) and the 8 new w values of the voxel as one 16-byte BF16
+// hi store and one lo store in the voxel-major w array.
+constexpr int UTV = 128, UQC = 8, UNB = 2, UNCW = 4;
+constexpr int UNT = 32 * (UNCW + 1);
+constexpr int UZW = UTV + 8, UNW = UTV + 4;
+
+struct UpdMaps {
+  CUtensorMap zc, zn, d, h, acc;
+};
+
+struct UpdArgs {
+  float* __restrict__ Zout;
+  float* __restrict__ Dout;
+  __nv_bfloat16* __restrict__ Whi;
+  __nv_bfloat16* __restrict__ Wlo;
+  double* __restrict__ partial;
+  int* __restrict__ err;
+  Grid g;
+  int Q, Qp, nqc;              // nqc = chunks per tile
+  int64_t T;                   // total chunks
+  float beta, xi, lam_s, inv_xb;
+};
+
+struct ULayout {
+  int zc, zn, dd, hh, aa, stage, bars, total;
+  __host__ __device__ ULayout(int NR) {
+    auto al = [](int b) { return (b + 127) / 128 * 128; };
+    zc = 0;
+    zn = al(UQC * UZW * 4);
+    dd = al(zn + NR * UQC * UNW * 4);
+    hh = dd + UQC * UTV * 4;
+    aa = hh + UQC * UTV * 4;
+    stage = al(aa + UQC * UTV * 4);
+    bars = UNB * stage;
+    total = bars + 4 * UNB * 8;
+  }
+};
+
+__host__ __device__ __forceinline__ int64_t ufloor4(int64_t v) {
+  return v >= 0 ? (v & ~(int64_t)3) : -(((-v) + 3) & ~(int64_t)3);
+}
+
+template <bool CHECK>
+__global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ UpdMaps maps,
+                                                        const UpdArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t ld = a.g.ld, N = a.g.N;
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const int NR = (ny > 1 ? 2 : 0) + (nz > 1 ? 2 : 0);
+  const ULayout L(NR);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint64_t* empty = full + UNB;
+  int64_t off[4] = {0, 0, 0, 0};
+  {
+    int k = 0;
+    if (ny > 1) { off[k++] = -(int64_t)nx; off[k++] = nx; }
+    if (nz > 1) { off[k++] = -(int64_t)nx * ny; off[k++] = (int64_t)nx * ny; }
+  }
+  const int64_t G = gridDim.x;
+  const int64_t lo = (a.T * (int64_t)blockIdx.x) / G, hi = (a.T * ((int64_t)blockIdx.x + 1)) / G;
+  const unsigned stage_bytes = (unsigned)(UQC * UZW * 4 + NR * UQC * UNW * 4 + 3 * UQC * UTV * 4);
+  if (tid == 0) {
+    for (int b = 0; b < UNB; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], UNCW);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  bool failed = false;
+  float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  if (warp == UNCW) {
+    if (lane == 0) {
+      tma_prefetch_map(&maps.zc);
+      for (int64_t c = lo; c < hi; ++c) {
+        const int i = (int)(c - lo), b = i % UNB, k = i / UNB;
+        if (i >= UNB && !mbar_wait(&empty[b], (k - 1) & 1)) {
+          failed = true;
+          break;
+        }
+        const int64_t tile = c / a.nqc;
+        const int q = (int)(c - tile * a.nqc) * UQC;
+        const int64_t n0 = tile * UTV;
+        unsigned char* st = smem + b * L.stage;
+        mbar_arrive_expect_tx(&full[b], stage_bytes);
+        tma_load_2d(st + L.zc, &maps.zc, (int)(n0 - 4), q, &full[b]);
+        for (int j = 0; j < NR; ++j)
+          tma_load_2d(st + L.zn + j * UQC * UNW * 4, &maps.zn, (int)ufloor4(n0 + off[j]), q,
+                      &full[b]);
+        tma_load_2d(st + L.dd, &maps.d, (int)n0, q, &full[b]);
+        tma_load_2d(st + L.hh, &maps.h, (int)n0, q, &full[b]);
+        tma_load_2d(st + L.aa, &maps.acc, (int)n0, q, &full[b]);
+      }
+    }
+  } else {
+    const int v = warp * 32 + lane;
+    for (int64_t c = lo; c < hi; ++c) {
+      const int i = (int)(c - lo), b = i % UNB, k = i / UNB;
+      if (!failed && !mbar_wait(&full[b], k & 1)) failed = true;
+      const int64_t tile = c / a.nqc;
+      const int q0 = (int)(c - tile * a.nqc) * UQC;
+      const int64_t n0 = tile * UTV, n = n0 + v;
+      const bool valid = n < N && !failed;
+      int x = 0, y = 0, zc = 0;
+      if (valid) {
+        x = (int)(n % nx);
+        const int64_t t = n / nx;
+        y = (int)(t % ny);
+        zc = (int)(t / ny);
+      }
+      const bool hxm = valid && x > 0, hxp = valid && x < nx - 1;
+      const bool hym = valid && y > 0, hyp = valid && y < ny - 1;
+      const bool hzm = valid && zc > 0, hzp = valid && zc < nz - 1;
+      const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
+      const bool flags[4] = {ny > 1 ? hym : hzm, ny > 1 ? hyp : hzp, hzm, hzp};
+      int nidx[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) nidx[j] = j < NR ? (int)(n + off[j] - ufloor4(n0 + off[j])) : 0;
+      const unsigned char* st = smem + b * L.stage;
+      const float* zr = reinterpret_cast<const float*>(st + L.zc);
+      const float* znr = reinterpret_cast<const float*>(st + L.zn);
+      const float* dr = reinterpret_cast<const float*>(st + L.dd);
+      const float* hr = reinterpret_cast<const float*>(st + L.hh);
+      const float* ar = reinterpret_cast<const float*>(st + L.aa);
+      float wv[UQC];
+#pragma unroll
+      for (int r = 0; r < UQC; ++r) {
+        wv[r] = 0.f;
+        const int q = q0 + r;
+        if (valid && q < a.Q) {
+          const float z = zr[r * UZW + 4 + v], d = dr[r * UTV + v];
+          float nb = 0.f;
+          if (hxm) nb += zr[r * UZW + 3 + v];
+          if (hxp) nb += zr[r * UZW + 5 + v];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j < NR && flags[j]) nb += znr[(j * UQC + r) * UNW + nidx[j]];
+          const float f = hr[r * UTV + v] + ar[r * UTV + v];
+          const float zn = fmaxf(0.f, (a.xi * z - a.lam_s * (deg * z - nb) + a.beta * f + d) * a.inv_xb);
+          const float dn = d - a.beta * (zn - f);
+          const int64_t o = (int64_t)q * ld + n;
+          a.Zout[o] = zn;
+          a.Dout[o] = dn;
+          wv[r] = a.beta * zn - dn;
+          if (CHECK) {
+            const float e = zn - f, ch = zn - z;
+            s1 = fmaf(e, e, s1);
+            s2 = fmaf(ch, ch, s2);
+            s3 = fmaf(zn, zn, s3);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[b]);
+      if (valid) {
+        uint32_t hh[4], ll[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float w0 = wv[2 * e], w1 = wv[2 * e + 1];
+          hh[e] = pack_bf16(w0, w1);
+          ll[e] = pack_bf16(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
+                            w1 - __bfloat162float(__float2bfloat16_rn(w1)));
+        }
+        *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+        *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+      }
+    }
+  }
+  if (failed) atomicExch(a.err, (int)SSM_ETIMEOUT);
+  if (CHECK) {
+    double d1 = s1, d2 = s2, d3 = s3;
+    for (int o = 16; o > 0; o >>= 1) {
+      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      d3 += __shfl_xor_sync(0xffffffffu, d3, o);
+    }
+    __shared__ double red[UNT / 32][3];
+    if (lane == 0) {
+      red[warp][0] = d1;
+      red[warp][1] = d2;
+      red[warp][2] = d3;
+    }
+    __syncthreads();
+    if (tid < 3) {
+      double t = 0.0;
+      for (int w = 0; w < UNT / 32; ++w) t += red[w][tid];
+      a.partial[(int64_t)blockIdx.x * 4 + tid] = t;
+    }
+  }
+}
+
+int g_nsm_tc = 0;
+
+int nsm() {
+  if (g_nsm_tc == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_nsm_tc, cudaDevAttrMultiProcessorCount, dev);
+    if (g_nsm_tc <= 0) g_nsm_tc = 148;
+  }
+  return g_nsm_tc;
+}
+
+int gemm_grid(const ssm_plan_s* pl) {
+  const int ntv = (int)((pl->g.N + BM - 1) / BM);
+  const int ntq = (pl->Q + BN - 1) / BN;
+  return std::max(1, std::min(nsm(), ntv * ntq));
+}
+
+int update_nr(const ssm_plan_s* pl) { return (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 ? 2 : 0); }
+
+int update_grid(const ssm_plan_s* pl) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    const size_t shm = (size_t)ULayout(4).total + 128;
+    cudaFuncSetAttribute(tc_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(tc_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_update_kernel<true>, UNT,
+                                                  (size_t)ULayout(update_nr(pl)).total + 128);
+    per_sm = std::max(1, b);
+  }
+  const int64_t ntiles = (pl->g.N + UTV - 1) / UTV;
+  const int64_t T = ntiles * ((pl->Q + UQC - 1) / UQC);
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm() * per_sm, T));
+}
+
+}  // namespace
 
 ssm_status tc_prepare(ssm_plan_s* pl, cudaStream_t s) {
-  (void)pl;
   (void)s;
-  set_error("the BF16X3 tensor-core form is not available in this build");
-  return SSM_EUNSUPPORTED;
+  if (pl->Qp % BK != 0) {
+    set_error("tensor-core form: padded Q must be a multiple of 64");
+    return SSM_EUNSUPPORTED;
+  }
+  SSM_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_BYTES));
+  update_grid(pl);
+  return SSM_OK;
 }
-ssm_status tc_iteration(ssm_plan_s*, int, bool, double*, int*, cudaStream_t) {
-  set_error("the BF16X3 tensor-core form is not available in this build");
-  return SSM_EUNSUPPORTED;
-}
+
+int tc_max_partials(const ssm_plan_s* pl) { return std::max(gemm_grid(pl), update_grid(pl)); }
+
 void tc_release(ssm_plan_s*) {}
-int tc_max_partials(const ssm_plan_s*) { return 1; }
+
+ssm_status tc_gemm(ssm_plan_s* pl, int cur, cudaStream_t s) {
+  const uint64_t Q = (uint64_t)pl->Q, N = (uint64_t)pl->g.N, Qp = (uint64_t)pl->Qp;
+  TcMaps m;
+  const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
+  SSM_CUDA(encode_2d(&m.a_hi, bf, 2, pl->Whi[cur], Q, N, Qp, BK, BM, sw));
+  SSM_CUDA(encode_2d(&m.a_lo, bf, 2, pl->Wlo[cur], Q, N, Qp, BK, BM, sw));
+  SSM_CUDA(encode_2d(&m.b_hi, bf, 2, pl->Mhi, Q, Q, Qp, BK, BN, sw));
+  SSM_CUDA(encode_2d(&m.b_lo, bf, 2, pl->Mlo, Q, Q, Qp, BK, BN, sw));
+  TcArgs a;
+  a.Acc = pl->Acc;
+  a.err = pl->dev_err;
+  a.g = pl->g;
+  a.Q = pl->Q;
+  a.ntv = (int)((pl->g.N + BM - 1) / BM);
+  a.ntq = (pl->Q + BN - 1) / BN;
+  tc_gemm_kernel<<<gemm_grid(pl), NTHR, SMEM_BYTES, s>>>(m, a);
+  SSM_LAUNCHED();
+  return SSM_OK;
+}
+
+ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
+                     cudaStream_t s) {
+  const uint64_t Q = (uint64_t)pl->Q, N = (uint64_t)pl->g.N, ld = (uint64_t)pl->g.ld;
+  UpdMaps m;
+  const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  SSM_CUDA(encode_2d(&m.zc, f32, 4, pl->Z[cur], N, Q, ld, UZW, UQC));
+  SSM_CUDA(encode_2d(&m.zn, f32, 4, pl->Z[cur], N, Q, ld, UNW, UQC));
+  SSM_CUDA(encode_2d(&m.d, f32, 4, pl->Dl[cur], N, Q, ld, UTV, UQC));
+  SSM_CUDA(encode_2d(&m.h, f32, 4, pl->H, N, Q, ld, UTV, UQC));
+  SSM_CUDA(encode_2d(&m.acc, f32, 4, pl->Acc, N, Q, ld, UTV, UQC));
+  UpdArgs a;
+  a.Zout = pl->Z[cur ^ 1];
+  a.Dout = pl->Dl[cur ^ 1];
+  a.Whi = pl->Whi[cur ^ 1];
+  a.Wlo = pl->Wlo[cur ^ 1];
+  a.partial = partial;
+  a.err = pl->dev_err;
+  a.g = pl->g;
+  a.Q = pl->Q;
+  a.Qp = pl->Qp;
+  a.nqc = (pl->Q + UQC - 1) / UQC;
+  a.T = ((pl->g.N + UTV - 1) / UTV) * (int64_t)a.nqc;
+  a.beta = (float)pl->p.beta;
+  a.xi = (float)pl->xi;
+  a.lam_s = (float)pl->lam_s;
+  a.inv_xb = (float)(1.0 / (pl->xi + pl->p.beta));
+  const int grid = update_grid(pl);
+  *nparts = grid;
+  const size_t shm = (size_t)ULayout(update_nr(pl)).total + 128;
+  if (check)
+    tc_update_kernel<true><<<grid, UNT, shm, s>>>(m, a);
+  else
+    tc_update_kernel<false><<<grid, UNT, shm, s>>>(m, a);
+  SSM_LAUNCHED();
+  return SSM_OK;
+}
+
+ssm_status tc_iteration(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
+                        cudaStream_t s) {
+  SSM_TRY(tc_gemm(pl, cur, s));
+  return tc_update(pl, cur, check, partial, nparts, s);
+}
 
 }  // namespace ssm
