@@ -154,6 +154,27 @@ ssm_status ssm_objective(ssm_plan_t plan, const float* M_dev, int64_t ldm,
                          double* J_host, void* stream);
 
 /*
+ * Objective of Eq. 7 / Eq. 8 without allocating any device memory and without a plan
+ * (the paper has no counterpart: this serves callers that cannot allocate -- e.g. a
+ * pipeline that forbids allocation once it runs, a process whose device memory is
+ * held by another allocator, or work on a busy device where cudaMalloc/cudaFree would
+ * synchronise it). Computes 1/2 ||M - K F||_F^2 + lambda * 1/2 ||D F||^2 from device
+ * buffers K (P x Q row-major floats), M (P x N, ldm) and F (Q x N, ldf) on the grid
+ * `dims` (ndim 1..3), with the stencil convention `stencil_pairs` (as in ssm_params);
+ * K F is FP32 with FP32 accumulation, both sums FP64. Writes *J_host and synchronises
+ * `stream`.
+ * Scratch: a fixed device array inside the library (256 KB per device, kept until
+ * the process exits) caps N at 4,194,304 voxels; larger grids get SSM_EINVAL. The
+ * first call on a device looks up that array's device address (with the device
+ * current), so make the first call before any stream capture. All calls share the
+ * array: calls that overlap on the GPU race. Nothing needs clearing between calls.
+ */
+ssm_status ssm_objective_noalloc(const float* K_dev, int P, int Q, const float* M_dev,
+                                 int64_t ldm, const float* F_dev, int64_t ldf, int ndim,
+                                 const int64_t* dims, double lambda, int stencil_pairs,
+                                 double* J_host, void* stream);
+
+/*
  * Read back the plan's factors (for tests): sigma (min(P,Q) doubles, descending) and,
  * when non-NULL, V_r (Q x r row-major doubles, the first r right singular vectors).
  */

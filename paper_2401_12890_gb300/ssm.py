@@ -87,6 +87,9 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_objective.argtypes = [vp, fp, i64, fp, i64, ctypes.c_int, dp, vp]
     lib.ssm_plan_factors.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     lib.ssm_destroy.argtypes = [vp]
+    lib.ssm_objective_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, i64, vp, i64,
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.c_double, ctypes.c_int, dp, vp]
     lib.ssm_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.ssm_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_status_string.argtypes = [ctypes.c_int]
@@ -95,7 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_launch_count.restype = ctypes.c_int64
     for name in ("ssm_default_params", "ssm_plan", "ssm_solve", "ssm_solve_host",
                  "ssm_objective", "ssm_plan_factors", "ssm_destroy", "ssm_profile_enable",
-                 "ssm_profile_read"):
+                 "ssm_profile_read", "ssm_objective_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
