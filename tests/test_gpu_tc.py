@@ -6,7 +6,7 @@ error is about 2^-16 ~ 1.5e-5; carried through the iteration this gives ~1e-5 af
 few iterations and ~1e-4 after 300 (the FP32 emulation of the same arithmetic gives
 1.4e-4 at 300 on the 32x32 workload). The bars: 1e-4 after <= 20 iterations, 1e-3
 after 300, and the objective of Eq. 7 within 1e-5 relative (where F is flat the
-objective is insensitive, which is why the spec bar is on the objective).
+objective is insensitive, so the bar at convergence is on the objective).
 """
 import numpy as np
 import pytest
@@ -76,7 +76,7 @@ def test_edge_cases_bf16x3(P, Q, dims, lam, beta):
 
 
 def test_objective_near_convergence_bf16x3():
-    # spec bar for the reduced-precision form: objective within 1e-4 of the
+    # the reduced-precision form at convergence: objective within 1e-4 of the
     # oracle's at convergence (3000 iterations leave the 32x32 problem's objective
     # within ~1e-6 of its limit; the oracle is run the same number of iterations)
     w = synth.WORKLOADS["dr2d_tiny"]
