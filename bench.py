@@ -186,7 +186,7 @@ def dominant_kernel(form, prec, Q, N, r):
                 8.0 * Q * N + 12.0 * r * N, "GB/s")
     if prec == "fp32":
         return ("sgemm_kernel", "ssm_dense.cu", "alu", 2.0 * Q * Q * N, "TFLOP/s")
-    return ("tc_dense_kernel", "ssm_tc.cu", "tensor", 3 * 2.0 * Q * Q * N, "TFLOP/s")
+    return ("tc_gemm_kernel", "ssm_tc.cu", "tensor", 3 * 2.0 * Q * Q * N, "TFLOP/s")
 
 
 # --------------------------------------------------------------------------------------

@@ -261,13 +261,15 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
 // ------------------------------------------------------------------------------------
 // tc_update_kernel: the z-step, dual step and next-w split, TMA-staged (HBM-bound)
 // ------------------------------------------------------------------------------------
-// A CTA owns a voxel tile of 128 and a contiguous share of the (tile, 8-compartment
-// chunk) list; one producer warp streams z (x halo), its -+nx (-+nx*ny) neighbour
+// Work items are (16-compartment chunk, voxel tile of 128) pairs ordered chunk-major, so
+// CTAs running at the same time hold the same compartments of neighbouring tiles and
+// the -+nx halo rows one CTA loads are the rows its neighbours load (L2 hits). A CTA
+// takes a contiguous share of the items; one producer warp streams z (x halo), its -+nx (-+nx*ny) neighbour
 // rows, d, h and acc for each chunk with 2D TMA boxes into a 2-stage mbarrier ring;
-// four consumer warps own a voxel per lane, compute the 8 compartments of the chunk,
-// store z' and d' (coalesced) and the 8 new w values of the voxel as one 16-byte BF16
-// hi store and one lo store in the voxel-major w array.
-constexpr int UTV = 128, UQC = 8, UNB = 2, UNCW = 4;
+// four consumer warps own a voxel per lane, compute the 16 compartments of the chunk,
+// store z' and d' (coalesced) and the 16 new w values of the voxel as one 32-byte BF16
+// hi/lo sector pair in the voxel-major w array.
+constexpr int UTV = 128, UQC = 16, UNB = 2, UNCW = 4;
 constexpr int UNT = 32 * (UNCW + 1);
 constexpr int UZW = UTV + 8, UNW = UTV + 4;
 
@@ -284,7 +286,7 @@ struct UpdArgs {
   int* __restrict__ err;
   Grid g;
   int Q, Qp, nqc;              // nqc = chunks per tile
-  int64_t T;                   // total chunks
+  int64_t ntiles, T;           // voxel tiles, total (chunk, tile) items
   float beta, xi, lam_s, inv_xb;
 };
 
@@ -348,8 +350,8 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
           failed = true;
           break;
         }
-        const int64_t tile = c / a.nqc;
-        const int q = (int)(c - tile * a.nqc) * UQC;
+        const int64_t tile = c % a.ntiles;
+        const int q = (int)(c / a.ntiles) * UQC;
         const int64_t n0 = tile * UTV;
         unsigned char* st = smem + b * L.stage;
         mbar_arrive_expect_tx(&full[b], stage_bytes);
@@ -367,8 +369,8 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
     for (int64_t c = lo; c < hi; ++c) {
       const int i = (int)(c - lo), b = i % UNB, k = i / UNB;
       if (!failed && !mbar_wait(&full[b], k & 1)) failed = true;
-      const int64_t tile = c / a.nqc;
-      const int q0 = (int)(c - tile * a.nqc) * UQC;
+      const int64_t tile = c % a.ntiles;
+      const int q0 = (int)(c / a.ntiles) * UQC;
       const int64_t n0 = tile * UTV, n = n0 + v;
       const bool valid = n < N && !failed;
       int x = 0, y = 0, zc = 0;
@@ -423,16 +425,22 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
       if (valid) {
-        uint32_t hh[4], ll[4];
+        // 16 values = one full 32-byte sector each for hi and lo
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float w0 = wv[2 * e], w1 = wv[2 * e + 1];
-          hh[e] = pack_bf16(w0, w1);
-          ll[e] = pack_bf16(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
-                            w1 - __bfloat162float(__float2bfloat16_rn(w1)));
+        for (int h2 = 0; h2 < UQC / 8; ++h2) {
+          uint32_t hh[4], ll[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float w0 = wv[8 * h2 + 2 * e], w1 = wv[8 * h2 + 2 * e + 1];
+            hh[e] = pack_bf16(w0, w1);
+            ll[e] = pack_bf16(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
+                              w1 - __bfloat162float(__float2bfloat16_rn(w1)));
+          }
+          *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0 + 8 * h2) =
+              make_uint4(hh[0], hh[1], hh[2], hh[3]);
+          *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0 + 8 * h2) =
+              make_uint4(ll[0], ll[1], ll[2], ll[3]);
         }
-        *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
-        *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
       }
     }
   }
@@ -555,7 +563,8 @@ ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* 
   a.Q = pl->Q;
   a.Qp = pl->Qp;
   a.nqc = (pl->Q + UQC - 1) / UQC;
-  a.T = ((pl->g.N + UTV - 1) / UTV) * (int64_t)a.nqc;
+  a.ntiles = (pl->g.N + UTV - 1) / UTV;
+  a.T = a.ntiles * (int64_t)a.nqc;
   a.beta = (float)pl->p.beta;
   a.xi = (float)pl->xi;
   a.lam_s = (float)pl->lam_s;
