@@ -164,6 +164,8 @@ ssm_status tc_prepare(ssm_plan_s* pl, cudaStream_t s);
 ssm_status tc_iteration(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
                         cudaStream_t s);
 ssm_status tc_gemm(ssm_plan_s* pl, int cur, cudaStream_t s);
+ssm_status tc_update_prepare(ssm_plan_s* pl);
+int tc_update_grid(const ssm_plan_s* pl);
 ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
                      cudaStream_t s);
 void tc_release(ssm_plan_s* pl);

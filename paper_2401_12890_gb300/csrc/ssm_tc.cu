@@ -4,7 +4,7 @@
 // once in FP64), h = M g (once per solve) and w = beta z - d. An iteration is two
 // kernels:
 //   tc_gemm_kernel    acc = M w on the tensor cores (tcgen05.mma, TMA-fed, FP32 in TMEM)
-//   tc_update_kernel  the bandwidth-bound rest, TMA-staged:
+//   tc_update_kernel  the bandwidth-bound rest, TMA-staged (ssm_tc_update.cu):
 //       f  = h + acc
 //       z' = max(0, (xi z - lambda s (deg z - sum_nbr z) + beta f + d) / (xi + beta))  (Eq. 31)
 //       d' = d - beta (z' - f)                                                      (step 11)
@@ -112,11 +112,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
-  return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
 }
 
 __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant__ TcMaps maps,
@@ -258,215 +253,6 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
   }
 }
 
-// ------------------------------------------------------------------------------------
-// tc_update_kernel: the z-step, dual step and next-w split, TMA-staged (HBM-bound)
-// ------------------------------------------------------------------------------------
-// Work items are (16-compartment chunk, voxel tile of 128) pairs ordered chunk-major, so
-// CTAs running at the same time hold the same compartments of neighbouring tiles and
-// the -+nx halo rows one CTA loads are the rows its neighbours load (L2 hits). A CTA
-// takes a contiguous share of the items; one producer warp streams z (x halo), its -+nx (-+nx*ny) neighbour
-// rows, d, h and acc for each chunk with 2D TMA boxes into a 2-stage mbarrier ring;
-// four consumer warps own a voxel per lane, compute the 16 compartments of the chunk,
-// store z' and d' (coalesced) and the 16 new w values of the voxel as one 32-byte BF16
-// hi/lo sector pair in the voxel-major w array.
-constexpr int UTV = 128, UQC = 16, UNB = 2, UNCW = 4;
-constexpr int UNT = 32 * (UNCW + 1);
-constexpr int UZW = UTV + 8, UNW = UTV + 4;
-
-struct UpdMaps {
-  CUtensorMap zc, zn, d, h, acc;
-};
-
-struct UpdArgs {
-  float* __restrict__ Zout;
-  float* __restrict__ Dout;
-  __nv_bfloat16* __restrict__ Whi;
-  __nv_bfloat16* __restrict__ Wlo;
-  double* __restrict__ partial;
-  int* __restrict__ err;
-  Grid g;
-  int Q, Qp, nqc;              // nqc = chunks per tile
-  int64_t ntiles, T;           // voxel tiles, total (chunk, tile) items
-  float beta, xi, lam_s, inv_xb;
-};
-
-struct ULayout {
-  int zc, zn, dd, hh, aa, stage, bars, total;
-  __host__ __device__ ULayout(int NR) {
-    auto al = [](int b) { return (b + 127) / 128 * 128; };
-    zc = 0;
-    zn = al(UQC * UZW * 4);
-    dd = al(zn + NR * UQC * UNW * 4);
-    hh = dd + UQC * UTV * 4;
-    aa = hh + UQC * UTV * 4;
-    stage = al(aa + UQC * UTV * 4);
-    bars = UNB * stage;
-    total = bars + 4 * UNB * 8;
-  }
-};
-
-__host__ __device__ __forceinline__ int64_t ufloor4(int64_t v) {
-  return v >= 0 ? (v & ~(int64_t)3) : -(((-v) + 3) & ~(int64_t)3);
-}
-
-template <bool CHECK>
-__global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ UpdMaps maps,
-                                                        const UpdArgs a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t ld = a.g.ld, N = a.g.N;
-  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const int NR = (ny > 1 ? 2 : 0) + (nz > 1 ? 2 : 0);
-  const ULayout L(NR);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
-  uint64_t* empty = full + UNB;
-  int64_t off[4] = {0, 0, 0, 0};
-  {
-    int k = 0;
-    if (ny > 1) { off[k++] = -(int64_t)nx; off[k++] = nx; }
-    if (nz > 1) { off[k++] = -(int64_t)nx * ny; off[k++] = (int64_t)nx * ny; }
-  }
-  const int64_t G = gridDim.x;
-  const int64_t lo = (a.T * (int64_t)blockIdx.x) / G, hi = (a.T * ((int64_t)blockIdx.x + 1)) / G;
-  const unsigned stage_bytes = (unsigned)(UQC * UZW * 4 + NR * UQC * UNW * 4 + 3 * UQC * UTV * 4);
-  if (tid == 0) {
-    for (int b = 0; b < UNB; ++b) {
-      mbar_init(&full[b], 1);
-      mbar_init(&empty[b], UNCW);
-    }
-    mbar_fence_init();
-  }
-  __syncthreads();
-  bool failed = false;
-  float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  if (warp == UNCW) {
-    if (lane == 0) {
-      tma_prefetch_map(&maps.zc);
-      for (int64_t c = lo; c < hi; ++c) {
-        const int i = (int)(c - lo), b = i % UNB, k = i / UNB;
-        if (i >= UNB && !mbar_wait(&empty[b], (k - 1) & 1)) {
-          failed = true;
-          break;
-        }
-        const int64_t tile = c % a.ntiles;
-        const int q = (int)(c / a.ntiles) * UQC;
-        const int64_t n0 = tile * UTV;
-        unsigned char* st = smem + b * L.stage;
-        mbar_arrive_expect_tx(&full[b], stage_bytes);
-        tma_load_2d(st + L.zc, &maps.zc, (int)(n0 - 4), q, &full[b]);
-        for (int j = 0; j < NR; ++j)
-          tma_load_2d(st + L.zn + j * UQC * UNW * 4, &maps.zn, (int)ufloor4(n0 + off[j]), q,
-                      &full[b]);
-        tma_load_2d(st + L.dd, &maps.d, (int)n0, q, &full[b]);
-        tma_load_2d(st + L.hh, &maps.h, (int)n0, q, &full[b]);
-        tma_load_2d(st + L.aa, &maps.acc, (int)n0, q, &full[b]);
-      }
-    }
-  } else {
-    const int v = warp * 32 + lane;
-    for (int64_t c = lo; c < hi; ++c) {
-      const int i = (int)(c - lo), b = i % UNB, k = i / UNB;
-      if (!failed && !mbar_wait(&full[b], k & 1)) failed = true;
-      const int64_t tile = c % a.ntiles;
-      const int q0 = (int)(c / a.ntiles) * UQC;
-      const int64_t n0 = tile * UTV, n = n0 + v;
-      const bool valid = n < N && !failed;
-      int x = 0, y = 0, zc = 0;
-      if (valid) {
-        x = (int)(n % nx);
-        const int64_t t = n / nx;
-        y = (int)(t % ny);
-        zc = (int)(t / ny);
-      }
-      const bool hxm = valid && x > 0, hxp = valid && x < nx - 1;
-      const bool hym = valid && y > 0, hyp = valid && y < ny - 1;
-      const bool hzm = valid && zc > 0, hzp = valid && zc < nz - 1;
-      const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
-      const bool flags[4] = {ny > 1 ? hym : hzm, ny > 1 ? hyp : hzp, hzm, hzp};
-      int nidx[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) nidx[j] = j < NR ? (int)(n + off[j] - ufloor4(n0 + off[j])) : 0;
-      const unsigned char* st = smem + b * L.stage;
-      const float* zr = reinterpret_cast<const float*>(st + L.zc);
-      const float* znr = reinterpret_cast<const float*>(st + L.zn);
-      const float* dr = reinterpret_cast<const float*>(st + L.dd);
-      const float* hr = reinterpret_cast<const float*>(st + L.hh);
-      const float* ar = reinterpret_cast<const float*>(st + L.aa);
-      float wv[UQC];
-#pragma unroll
-      for (int r = 0; r < UQC; ++r) {
-        wv[r] = 0.f;
-        const int q = q0 + r;
-        if (valid && q < a.Q) {
-          const float z = zr[r * UZW + 4 + v], d = dr[r * UTV + v];
-          float nb = 0.f;
-          if (hxm) nb += zr[r * UZW + 3 + v];
-          if (hxp) nb += zr[r * UZW + 5 + v];
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (j < NR && flags[j]) nb += znr[(j * UQC + r) * UNW + nidx[j]];
-          const float f = hr[r * UTV + v] + ar[r * UTV + v];
-          const float zn = fmaxf(0.f, (a.xi * z - a.lam_s * (deg * z - nb) + a.beta * f + d) * a.inv_xb);
-          const float dn = d - a.beta * (zn - f);
-          const int64_t o = (int64_t)q * ld + n;
-          a.Zout[o] = zn;
-          a.Dout[o] = dn;
-          wv[r] = a.beta * zn - dn;
-          if (CHECK) {
-            const float e = zn - f, ch = zn - z;
-            s1 = fmaf(e, e, s1);
-            s2 = fmaf(ch, ch, s2);
-            s3 = fmaf(zn, zn, s3);
-          }
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[b]);
-      if (valid) {
-        // 16 values = one full 32-byte sector each for hi and lo
-#pragma unroll
-        for (int h2 = 0; h2 < UQC / 8; ++h2) {
-          uint32_t hh[4], ll[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float w0 = wv[8 * h2 + 2 * e], w1 = wv[8 * h2 + 2 * e + 1];
-            hh[e] = pack_bf16(w0, w1);
-            ll[e] = pack_bf16(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
-                              w1 - __bfloat162float(__float2bfloat16_rn(w1)));
-          }
-          *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0 + 8 * h2) =
-              make_uint4(hh[0], hh[1], hh[2], hh[3]);
-          *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0 + 8 * h2) =
-              make_uint4(ll[0], ll[1], ll[2], ll[3]);
-        }
-      }
-    }
-  }
-  if (failed) atomicExch(a.err, (int)SSM_ETIMEOUT);
-  if (CHECK) {
-    double d1 = s1, d2 = s2, d3 = s3;
-    for (int o = 16; o > 0; o >>= 1) {
-      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-      d3 += __shfl_xor_sync(0xffffffffu, d3, o);
-    }
-    __shared__ double red[UNT / 32][3];
-    if (lane == 0) {
-      red[warp][0] = d1;
-      red[warp][1] = d2;
-      red[warp][2] = d3;
-    }
-    __syncthreads();
-    if (tid < 3) {
-      double t = 0.0;
-      for (int w = 0; w < UNT / 32; ++w) t += red[w][tid];
-      a.partial[(int64_t)blockIdx.x * 4 + tid] = t;
-    }
-  }
-}
-
 int g_nsm_tc = 0;
 
 int nsm() {
@@ -485,24 +271,6 @@ int gemm_grid(const ssm_plan_s* pl) {
   return std::max(1, std::min(nsm(), ntv * ntq));
 }
 
-int update_nr(const ssm_plan_s* pl) { return (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 ? 2 : 0); }
-
-int update_grid(const ssm_plan_s* pl) {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    const size_t shm = (size_t)ULayout(4).total + 128;
-    cudaFuncSetAttribute(tc_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    cudaFuncSetAttribute(tc_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_update_kernel<true>, UNT,
-                                                  (size_t)ULayout(update_nr(pl)).total + 128);
-    per_sm = std::max(1, b);
-  }
-  const int64_t ntiles = (pl->g.N + UTV - 1) / UTV;
-  const int64_t T = ntiles * ((pl->Q + UQC - 1) / UQC);
-  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm() * per_sm, T));
-}
-
 }  // namespace
 
 ssm_status tc_prepare(ssm_plan_s* pl, cudaStream_t s) {
@@ -513,11 +281,10 @@ ssm_status tc_prepare(ssm_plan_s* pl, cudaStream_t s) {
   }
   SSM_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 SMEM_BYTES));
-  update_grid(pl);
-  return SSM_OK;
+  return tc_update_prepare(pl);
 }
 
-int tc_max_partials(const ssm_plan_s* pl) { return std::max(gemm_grid(pl), update_grid(pl)); }
+int tc_max_partials(const ssm_plan_s* pl) { return std::max(gemm_grid(pl), tc_update_grid(pl)); }
 
 void tc_release(ssm_plan_s*) {}
 
@@ -538,44 +305,6 @@ ssm_status tc_gemm(ssm_plan_s* pl, int cur, cudaStream_t s) {
   a.ntv = (int)((pl->g.N + BM - 1) / BM);
   a.ntq = (pl->Q + BN - 1) / BN;
   tc_gemm_kernel<<<gemm_grid(pl), NTHR, SMEM_BYTES, s>>>(m, a);
-  SSM_LAUNCHED();
-  return SSM_OK;
-}
-
-ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
-                     cudaStream_t s) {
-  const uint64_t Q = (uint64_t)pl->Q, N = (uint64_t)pl->g.N, ld = (uint64_t)pl->g.ld;
-  UpdMaps m;
-  const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  SSM_CUDA(encode_2d(&m.zc, f32, 4, pl->Z[cur], N, Q, ld, UZW, UQC));
-  SSM_CUDA(encode_2d(&m.zn, f32, 4, pl->Z[cur], N, Q, ld, UNW, UQC));
-  SSM_CUDA(encode_2d(&m.d, f32, 4, pl->Dl[cur], N, Q, ld, UTV, UQC));
-  SSM_CUDA(encode_2d(&m.h, f32, 4, pl->H, N, Q, ld, UTV, UQC));
-  SSM_CUDA(encode_2d(&m.acc, f32, 4, pl->Acc, N, Q, ld, UTV, UQC));
-  UpdArgs a;
-  a.Zout = pl->Z[cur ^ 1];
-  a.Dout = pl->Dl[cur ^ 1];
-  a.Whi = pl->Whi[cur ^ 1];
-  a.Wlo = pl->Wlo[cur ^ 1];
-  a.partial = partial;
-  a.err = pl->dev_err;
-  a.g = pl->g;
-  a.Q = pl->Q;
-  a.Qp = pl->Qp;
-  a.nqc = (pl->Q + UQC - 1) / UQC;
-  a.ntiles = (pl->g.N + UTV - 1) / UTV;
-  a.T = a.ntiles * (int64_t)a.nqc;
-  a.beta = (float)pl->p.beta;
-  a.xi = (float)pl->xi;
-  a.lam_s = (float)pl->lam_s;
-  a.inv_xb = (float)(1.0 / (pl->xi + pl->p.beta));
-  const int grid = update_grid(pl);
-  *nparts = grid;
-  const size_t shm = (size_t)ULayout(update_nr(pl)).total + 128;
-  if (check)
-    tc_update_kernel<true><<<grid, UNT, shm, s>>>(m, a);
-  else
-    tc_update_kernel<false><<<grid, UNT, shm, s>>>(m, a);
   SSM_LAUNCHED();
   return SSM_OK;
 }
