@@ -49,7 +49,8 @@ typedef enum {
   SSM_ENAN = 4,            /* a residual became NaN or Inf                          */
   SSM_ETIMEOUT = 5,        /* a bounded device-side wait gave up                    */
   SSM_EUNSUPPORTED = 6,    /* valid request outside what this build implements      */
-  SSM_ENOTCONVERGED = 7    /* tolerance set but not reached within max_iter (info)  */
+  SSM_ENOTCONVERGED = 7,   /* tolerance set but not reached within max_iter (info)  */
+  SSM_EPENDING = 8         /* a served request has not finished yet                 */
 } ssm_status;
 
 typedef enum {
@@ -194,8 +195,127 @@ ssm_status ssm_profile_enable(ssm_plan_t plan, int enable);
 ssm_status ssm_profile_read(ssm_plan_t plan, double* main_kernel_ms,
                             int64_t* main_kernel_launches);
 
+/*
+ * Replay the solve loop's iteration blocks as CUDA graphs (launch-overhead support, no
+ * counterpart in the paper). A block is the run of iterations up to the next residual
+ * test, or 64 iterations when no test comes sooner; each distinct block (start parity,
+ * length, test pattern) is captured once on the plan and replayed by later blocks and
+ * later solves. Results are bitwise the same as with direct launches. Graphs are used
+ * only on a stream other than the legacy default stream, when the stream is not already
+ * being captured, and when profiling is off; otherwise launches are issued directly.
+ */
+ssm_status ssm_plan_set_graphs(ssm_plan_t plan, int enable);
+
+/*
+ * Device memory a plan for `p` would take on `device`, from the same sizes ssm_plan
+ * allocates: *persistent_bytes = what the plan holds between calls, including the
+ * staging buffers of ssm_solve_host; *peak_bytes = that plus the temporaries of
+ * planning. For the low-rank form without a fixed rank the bound assumes the largest
+ * supported rank, min(P, Q, 64). Allocates nothing.
+ */
+ssm_status ssm_plan_footprint(const ssm_params* p, int device, int64_t* persistent_bytes,
+                              int64_t* peak_bytes);
+
+/* Device bytes the plan currently holds (every allocation it owns). */
+ssm_status ssm_plan_device_bytes(ssm_plan_t plan, int64_t* bytes);
+
 /* Free everything the plan owns. NULL is accepted. Synchronises the plan's device. */
 ssm_status ssm_destroy(ssm_plan_t plan);
+
+/*
+ * ------------------------------------------------------------------------------------
+ * Serving: continuous batching of independent solves on one device (no counterpart in
+ * the paper, which fits one data set at a time).
+ *
+ * A server owns `max_active` workers, each a host thread with its own CUDA stream.
+ * Requests are admitted while a worker is free and the request's device footprint
+ * (ssm_plan_footprint, peak) fits in what remains of the HBM budget. Admission is
+ * first-come first-served; a later request may pass a waiting one that does not fit
+ * yet ("backfill"), but at most `max_bypass` times, after which admission waits for
+ * memory to free up. Admitted solves run concurrently on their streams, so their
+ * kernels overlap on the GPU. With `cache_plans`, a finished solve's plan (factors and
+ * state) stays resident; a later request with the same K, grid and plan parameters
+ * (all of ssm_params except max_iter, check_every, tol_primal and tol_change) reuses
+ * it without planning again. Idle plans are evicted least recently used first when a
+ * new request needs their memory. Each request's result is exactly what ssm_solve_host
+ * gives for it alone: the kernels and launch shapes do not depend on what else runs.
+ * ------------------------------------------------------------------------------------
+ */
+typedef struct ssm_server_s* ssm_server_t;
+
+typedef struct {
+  int device;              /* CUDA device the server runs on                        */
+  int max_active;          /* solves in flight at once, >= 1                         */
+  int64_t hbm_budget;      /* device bytes the server may hold in plans; <= 0 selects
+                              90 % of the device's free memory at creation          */
+  int use_graphs;          /* replay iteration blocks as CUDA graphs                 */
+  int cache_plans;         /* keep idle plans resident for reuse                     */
+  int max_bypass;          /* passes of a waiting request by later ones; < 0 selects
+                              2 * max_active                                        */
+  int64_t simulate_us;     /* > 0: scheduler test mode. Nothing is planned and no GPU
+                              work is issued; an admitted request holds its slot and
+                              its footprint for max_iter * simulate_us microseconds,
+                              leaves F untouched and finishes with SSM_OK and 0
+                              iterations. 0 = normal operation                      */
+} ssm_server_config;
+
+typedef struct {
+  int status;              /* ssm_status of the solve                               */
+  int iterations;          /* iterations run                                        */
+  double res_primal;       /* residuals at the last test (-1: none)                 */
+  double res_change;
+  double queue_ms;         /* submit -> admitted                                    */
+  double plan_ms;          /* host time spent planning (0 when a plan was reused)   */
+  double solve_ms;         /* admitted -> F_host written (planning included)        */
+  double latency_ms;       /* submit -> F_host written                              */
+  int64_t footprint;       /* device bytes reserved at admission (peak estimate)    */
+  int64_t order;           /* admission sequence number, from 0                     */
+  int slot;                /* worker that ran the solve                             */
+  int plan_reused;         /* 1 if a resident plan was reused                       */
+} ssm_request_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, rejected;
+  int64_t plans_created, plans_reused, plans_evicted;
+  int64_t bytes_held;      /* reserved now: running requests and resident plans     */
+  int64_t peak_bytes_held; /* largest reservation seen (never above hbm_budget)     */
+  int64_t budget;          /* the HBM budget in force                               */
+  int active, pending;     /* requests running / waiting now                        */
+} ssm_server_stats;
+
+/* Defaults: device 0, 4 workers, 90 % of free memory, graphs on, plan cache on,
+ * max_bypass 2 * max_active, normal operation. */
+ssm_status ssm_server_default_config(ssm_server_config* c);
+
+/* Create a server (threads and streams start here). */
+ssm_status ssm_server_create(ssm_server_t* out, const ssm_server_config* c);
+
+/*
+ * Queue one solve. K_host (P x Q doubles), M_host (P x N floats, ldm) and F_host
+ * (Q x N floats, ldf) are the caller's and must stay valid until ssm_server_wait or
+ * ssm_server_poll reports the request finished: K and M are read after admission, F
+ * is written at the end. *ticket identifies the request. Returns SSM_EINVAL for bad
+ * parameters and SSM_ENOMEM (nothing queued) when the request's footprint exceeds the
+ * whole budget.
+ */
+ssm_status ssm_server_submit(ssm_server_t s, const ssm_params* p, const double* K_host,
+                             const float* M_host, int64_t ldm, float* F_host, int64_t ldf,
+                             int64_t* ticket);
+
+/* SSM_OK and *info filled (the solve's own status in info->status) once the request
+ * has finished, after which the ticket is released; SSM_EPENDING while it has not;
+ * SSM_EINVAL for an unknown ticket. */
+ssm_status ssm_server_poll(ssm_server_t s, int64_t ticket, ssm_request_info* info);
+
+/* As ssm_server_poll, blocking up to timeout_ms (< 0: no limit). */
+ssm_status ssm_server_wait(ssm_server_t s, int64_t ticket, double timeout_ms,
+                           ssm_request_info* info);
+
+ssm_status ssm_server_stats_read(ssm_server_t s, ssm_server_stats* out);
+
+/* Wait for every submitted request to finish, stop the workers and free every plan.
+ * Tickets not yet collected become invalid. NULL is accepted. */
+ssm_status ssm_server_destroy(ssm_server_t s);
 
 /* Static description of a status code. */
 const char* ssm_status_string(int status);

@@ -14,9 +14,30 @@
 namespace ssm {
 
 std::atomic<int64_t> g_launches{0};
+thread_local int64_t t_launches = 0;
 static thread_local std::string t_last_error;
 
 void set_error(const std::string& msg) { t_last_error = msg; }
+
+int sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
+    int a = 0;
+    if (cudaDeviceGetAttribute(&a, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || a <= 0)
+      a = 148;
+    v = a;
+    cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
+std::mutex& attr_mutex() {
+  static std::mutex m;
+  return m;
+}
 
 cudaError_t encode_2d(CUtensorMap* map, CUtensorMapDataType dtype, size_t elem, const void* base,
                       uint64_t cols, uint64_t rows, uint64_t ld, unsigned box_cols,
@@ -73,6 +94,14 @@ ssm_status dalloc(T** p, size_t count, cudaStream_t s) {
   *p = nullptr;
   if (count == 0) return SSM_OK;
   SSM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(T) * count, s));
+  return SSM_OK;
+}
+
+// an allocation the plan owns: counted in pl->bytes
+template <typename T>
+ssm_status palloc(ssm_plan_s* pl, T** p, size_t count, cudaStream_t s) {
+  SSM_TRY(dalloc(p, count, s));
+  pl->bytes += (int64_t)(sizeof(T) * count);
   return SSM_OK;
 }
 
@@ -173,6 +202,8 @@ void release(ssm_plan_s* pl) {
   if (pl->ev0) cudaEventDestroy(pl->ev0);
   if (pl->ev1) cudaEventDestroy(pl->ev1);
   for (cudaEvent_t e : pl->prof_ev) cudaEventDestroy(e);
+  for (GraphBlock& b : pl->graphs)
+    if (b.exec) cudaGraphExecDestroy(b.exec);
   delete pl;
 }
 
@@ -197,7 +228,7 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   const int n = pl->n;
 
   // dictionary and its Gram eigendecomposition (FP64)
-  SSM_TRY(dalloc(&pl->K64, (size_t)P * Q, s));
+  SSM_TRY(palloc(pl, &pl->K64, (size_t)P * Q, s));
   SSM_CUDA(cudaMemcpyAsync(pl->K64, K_host, sizeof(double) * P * Q, cudaMemcpyHostToDevice, s));
   double *A = nullptr, *E = nullptr, *scratch = nullptr;
   SSM_TRY(dalloc(&A, (size_t)n * n, s));
@@ -253,22 +284,22 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   }
   pl->Qp = (int)round_up(Q, 64);
 
-  SSM_TRY(dalloc(&pl->Bp64, (size_t)P * n, s));
-  SSM_TRY(dalloc(&pl->Kt64, (size_t)Q * n, s));
-  SSM_TRY(dalloc(&pl->sig64, (size_t)n, s));
-  SSM_TRY(dalloc(&pl->alpha64, (size_t)n, s));
-  SSM_TRY(dalloc(&pl->K32, (size_t)P * Q, s));
-  SSM_TRY(dalloc(&pl->Kr32, (size_t)P * Q, s));
+  SSM_TRY(palloc(pl, &pl->Bp64, (size_t)P * n, s));
+  SSM_TRY(palloc(pl, &pl->Kt64, (size_t)Q * n, s));
+  SSM_TRY(palloc(pl, &pl->sig64, (size_t)n, s));
+  SSM_TRY(palloc(pl, &pl->alpha64, (size_t)n, s));
+  SSM_TRY(palloc(pl, &pl->K32, (size_t)P * Q, s));
+  SSM_TRY(palloc(pl, &pl->Kr32, (size_t)P * Q, s));
   if (p.form == SSM_FORM_LOWRANK) {
-    SSM_TRY(dalloc(&pl->V32, (size_t)Q * pl->R, s));
-    SSM_TRY(dalloc(&pl->coefA, (size_t)pl->R, s));
-    SSM_TRY(dalloc(&pl->coefW, (size_t)pl->R, s));
+    SSM_TRY(palloc(pl, &pl->V32, (size_t)Q * pl->R, s));
+    SSM_TRY(palloc(pl, &pl->coefA, (size_t)pl->R, s));
+    SSM_TRY(palloc(pl, &pl->coefW, (size_t)pl->R, s));
   } else {
-    SSM_TRY(dalloc(&pl->Gq32, (size_t)Q * n, s));
-    SSM_TRY(dalloc(&pl->Mq32, (size_t)Q * pl->Qp, s));
+    SSM_TRY(palloc(pl, &pl->Gq32, (size_t)Q * n, s));
+    SSM_TRY(palloc(pl, &pl->Mq32, (size_t)Q * pl->Qp, s));
     if (p.precision == SSM_BF16X3) {
-      SSM_TRY(dalloc(&pl->Mhi, (size_t)Q * pl->Qp, s));
-      SSM_TRY(dalloc(&pl->Mlo, (size_t)Q * pl->Qp, s));
+      SSM_TRY(palloc(pl, &pl->Mhi, (size_t)Q * pl->Qp, s));
+      SSM_TRY(palloc(pl, &pl->Mlo, (size_t)Q * pl->Qp, s));
     }
   }
   st = factors_fp64(pl, E, s);
@@ -281,30 +312,30 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   // per-voxel state
   const size_t QN = (size_t)Q * pl->g.ld;
   for (int i = 0; i < 2; ++i) {
-    SSM_TRY(dalloc(&pl->Z[i], QN, s));
-    SSM_TRY(dalloc(&pl->Dl[i], QN, s));
+    SSM_TRY(palloc(pl, &pl->Z[i], QN, s));
+    SSM_TRY(palloc(pl, &pl->Dl[i], QN, s));
   }
   int maxparts = 1;
   if (p.form == SSM_FORM_LOWRANK) {
-    SSM_TRY(dalloc(&pl->S, (size_t)pl->R * pl->g.ld, s));
+    SSM_TRY(palloc(pl, &pl->S, (size_t)pl->R * pl->g.ld, s));
     pl->lr_grid = lowrank_grid(pl);
     const size_t pf = (size_t)lowrank_partial_floats(pl, pl->lr_grid);
-    for (int i = 0; i < 2; ++i) SSM_TRY(dalloc(&pl->U[i], pf, s));
+    for (int i = 0; i < 2; ++i) SSM_TRY(palloc(pl, &pl->U[i], pf, s));
     maxparts = lowrank_max_partials(pl);
   } else {
-    SSM_TRY(dalloc(&pl->C32, (size_t)n * pl->g.ld, s));
-    SSM_TRY(dalloc(&pl->H, QN, s));
+    SSM_TRY(palloc(pl, &pl->C32, (size_t)n * pl->g.ld, s));
+    SSM_TRY(palloc(pl, &pl->H, QN, s));
     if (p.precision == SSM_FP32) {
-      SSM_TRY(dalloc(&pl->Wf, QN, s));
-      SSM_TRY(dalloc(&pl->Acc, QN, s));
+      SSM_TRY(palloc(pl, &pl->Wf, QN, s));
+      SSM_TRY(palloc(pl, &pl->Acc, QN, s));
       maxparts = dense_max_partials(pl);
     } else {
       // w for the tensor-core operand: voxel-major rows of Qp compartments
       const size_t WN = (size_t)pl->g.ld * pl->Qp;
-      SSM_TRY(dalloc(&pl->Acc, QN, s));
+      SSM_TRY(palloc(pl, &pl->Acc, QN, s));
       for (int i = 0; i < 2; ++i) {
-        SSM_TRY(dalloc(&pl->Whi[i], WN, s));
-        SSM_TRY(dalloc(&pl->Wlo[i], WN, s));
+        SSM_TRY(palloc(pl, &pl->Whi[i], WN, s));
+        SSM_TRY(palloc(pl, &pl->Wlo[i], WN, s));
       }
       SSM_TRY(tc_prepare(pl, s));
       maxparts = std::max(tc_max_partials(pl), dense_max_partials(pl));
@@ -312,14 +343,90 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   }
   maxparts = std::max(maxparts, (int)((pl->g.N + 255) / 256));  // objective partials
   pl->red_cap = maxparts;
-  SSM_TRY(dalloc(&pl->red, (size_t)maxparts * 4, s));
-  SSM_TRY(dalloc(&pl->red_out, 4, s));
-  SSM_TRY(dalloc(&pl->dev_err, 1, s));
+  SSM_TRY(palloc(pl, &pl->red, (size_t)maxparts * 4, s));
+  SSM_TRY(palloc(pl, &pl->red_out, 4, s));
+  SSM_TRY(palloc(pl, &pl->dev_err, 1, s));
   SSM_CUDA(cudaMemsetAsync(pl->dev_err, 0, sizeof(int), s));
   SSM_CUDA(cudaMallocHost(&pl->red_host, 4 * sizeof(double)));
   SSM_CUDA(cudaEventRecord(pl->ev1, s));
   SSM_CUDA(cudaEventSynchronize(pl->ev1));
   SSM_CUDA(cudaEventElapsedTime(&pl->plan_ms, pl->ev0, pl->ev1));
+  return SSM_OK;
+}
+
+// Device bytes a plan for `p` takes, following plan_impl allocation by allocation:
+// `persistent` = what the plan holds between calls (with the staging buffers of
+// ssm_solve_host when `staging`), `peak` = persistent plus planning's temporaries
+// (Gram matrix, eigenvectors, Jacobi scratch, K_r and the FP64 inverse). The low-rank
+// rank is known only after the eigendecomposition: without a fixed rank the bound
+// takes r = min(P, Q, 64), the largest the low-rank kernel supports.
+ssm_status footprint_impl(const ssm_params& p, bool staging, int64_t* persistent, int64_t* peak) {
+  ssm_plan_s t;
+  t.p = p;
+  t.P = p.P;
+  t.Q = p.Q;
+  t.g.nx = (int)p.dims[0];
+  t.g.ny = p.ndim >= 2 ? (int)p.dims[1] : 1;
+  t.g.nz = p.ndim >= 3 ? (int)p.dims[2] : 1;
+  t.g.N = (int64_t)t.g.nx * t.g.ny * t.g.nz;
+  t.g.ld = round_up(t.g.N, 128);
+  t.n = std::min(p.P, p.Q);
+  const int64_t P = p.P, Q = p.Q, n = t.n, ld = t.g.ld;
+  t.Qp = (int)round_up(Q, 64);
+  if (p.form == SSM_FORM_LOWRANK) {
+    t.r = p.rank > 0 ? std::min(p.rank, t.n) : std::min(t.n, kMaxRank);
+    t.R = padded_rank(t.r);
+    if (t.R < 0) {
+      set_error("low-rank form supports r <= 64; use the dense form for higher ranks");
+      return SSM_EUNSUPPORTED;
+    }
+  }
+  int64_t b = 0;
+  auto add = [&](int64_t elem, int64_t count) { b += elem * count; };
+  add(8, P * Q);                              // K64
+  add(8, P * n);                              // Bp64
+  add(8, Q * n);                              // Kt64
+  add(8, n);                                  // sig64
+  add(8, n);                                  // alpha64
+  add(4, P * Q);                              // K32
+  add(4, P * Q);                              // Kr32
+  if (p.form == SSM_FORM_LOWRANK) {
+    add(4, Q * t.R);                          // V32
+    add(4, 2 * (int64_t)t.R);                 // coefA, coefW
+  } else {
+    add(4, Q * n);                            // Gq32
+    add(4, Q * t.Qp);                         // Mq32
+    if (p.precision == SSM_BF16X3) add(2, 2 * Q * t.Qp);  // Mhi, Mlo
+  }
+  const int64_t QN = Q * ld;
+  add(4, 4 * QN);                             // Z[2], Dl[2]
+  int64_t maxparts = 1;
+  if (p.form == SSM_FORM_LOWRANK) {
+    add(4, (int64_t)t.R * ld);                // S
+    t.lr_grid = lowrank_grid(&t);
+    add(4, 2 * lowrank_partial_floats(&t, t.lr_grid));  // U[2]
+    maxparts = lowrank_max_partials(&t);
+  } else {
+    add(4, n * ld);                           // C32
+    add(4, QN);                               // H
+    if (p.precision == SSM_FP32) {
+      add(4, 2 * QN);                         // Wf, Acc
+      maxparts = dense_max_partials(&t);
+    } else {
+      add(4, QN);                             // Acc
+      add(2, 4 * ld * t.Qp);                  // Whi[2], Wlo[2]
+      maxparts = std::max(tc_max_partials(&t), dense_max_partials(&t));
+    }
+  }
+  maxparts = std::max<int64_t>(maxparts, (t.g.N + 255) / 256);
+  add(8, maxparts * 4);                       // red
+  add(8, 4);                                  // red_out
+  add(4, 1);                                  // dev_err
+  if (staging) add(4, (P + Q) * ld);          // Mstage, Fstage
+  *persistent = b;
+  int64_t tmp = 8 * (3 * n * n + 2) + 4 * n + 8 * P * Q;  // A, E, scratch, perm, K_r
+  if (p.form == SSM_FORM_DENSE) tmp += 8 * (n + Q * Q);   // inverse weights, FP64 inverse
+  *peak = b + tmp;
   return SSM_OK;
 }
 
@@ -392,6 +499,81 @@ ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, bool check_next, i
   return tc_update(pl, cur, check, pl->red, nparts, s);
 }
 
+// iterations per block when no residual test ends it earlier
+constexpr int kBlockMax = 64;
+
+// a stream that can be captured: not the legacy default stream, not already capturing
+bool capturable(cudaStream_t s) {
+  if (s == nullptr || s == cudaStreamLegacy) return false;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st == cudaStreamCaptureStatusNone;
+}
+
+// iterations k .. k+L-1 as direct launches; *nparts = partial rows of the last test
+template <typename IsCheck>
+ssm_status run_block(ssm_plan_s* pl, int cur, int k, int L, const IsCheck& is_check, int* nparts,
+                     cudaStream_t s) {
+  for (int j = k; j < k + L; ++j) {
+    int np = 0;
+    SSM_TRY(one_iteration(pl, cur, is_check(j), is_check(j + 1), &np, s));
+    if (is_check(j)) *nparts = np;
+    cur ^= 1;
+  }
+  return SSM_OK;
+}
+
+// the same block replayed from a graph captured on its first use; the graph bakes in
+// the plan's buffers and the block's pattern of residual tests, both fixed for a plan
+template <typename IsCheck>
+ssm_status run_block_graph(ssm_plan_s* pl, int cur, int k, int L, const IsCheck& is_check,
+                           int* nparts, cudaStream_t s) {
+  std::string key;
+  key.reserve(2 * L + 8);
+  key += (char)cur;
+  key += std::to_string(L);
+  key += ':';
+  for (int j = k; j < k + L; ++j) key += (char)('0' + (is_check(j) ? 1 : 0) + (is_check(j + 1) ? 2 : 0));
+  GraphBlock* blk = nullptr;
+  for (GraphBlock& b : pl->graphs)
+    if (b.key == key) blk = &b;
+  if (!blk) {
+    SSM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int64_t t0 = t_launches;
+    int np = 0;
+    const ssm_status st = run_block(pl, cur, k, L, is_check, &np, s);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    const int64_t captured = t_launches - t0;
+    g_launches.fetch_sub(captured, std::memory_order_relaxed);  // counted when replayed
+    t_launches -= captured;
+    if (st != SSM_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (st != SSM_OK) return st;
+      SSM_CUDA(e);
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    SSM_CUDA(ei);
+    GraphBlock b;
+    b.key = key;
+    b.exec = exec;
+    b.kernels = captured;
+    b.nparts = np;
+    pl->graphs.push_back(std::move(b));
+    blk = &pl->graphs.back();
+  }
+  SSM_CUDA(cudaGraphLaunch(blk->exec, s));
+  g_launches.fetch_add(blk->kernels, std::memory_order_relaxed);
+  t_launches += blk->kernels;
+  *nparts = blk->nparts;
+  return SSM_OK;
+}
+
 ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int64_t ldf,
                       ssm_info* info, cudaStream_t s) {
   const ssm_params& p = pl->p;
@@ -432,15 +614,25 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
     const bool at = p.check_every > 0 && ((j + 1) % p.check_every == 0);
     return (use_tol && at) || j + 1 == p.max_iter;
   };
+  const bool graphs = pl->use_graphs && !pl->prof_enabled && capturable(s);
+  // blocks of iterations end at each residual test (the host reads the sums there) or
+  // after kBlockMax iterations; a block runs as direct launches or as one graph replay
   while (k < p.max_iter) {
-    const bool at_check = p.check_every > 0 && ((k + 1) % p.check_every == 0);
-    const bool check = is_check(k);
+    int L = 0;
+    while (k + L < p.max_iter && L < kBlockMax) {
+      ++L;
+      if (is_check(k + L - 1)) break;
+    }
     int nparts = 0;
-    SSM_TRY(one_iteration(pl, cur, check, is_check(k + 1), &nparts, s));
-    cur ^= 1;
-    ++k;
-    if (check) {
+    if (graphs)
+      SSM_TRY(run_block_graph(pl, cur, k, L, is_check, &nparts, s));
+    else
+      SSM_TRY(run_block(pl, cur, k, L, is_check, &nparts, s));
+    cur ^= (L & 1);
+    k += L;
+    if (is_check(k - 1)) {
       SSM_TRY(read_residuals(pl, nparts, s, &rp, &rc));
+      const bool at_check = p.check_every > 0 && (k % p.check_every == 0);
       if (use_tol && at_check) {
         const bool ok_p = p.tol_primal <= 0 || rp <= p.tol_primal;
         const bool ok_c = p.tol_change <= 0 || rc <= p.tol_change;
@@ -472,6 +664,13 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
 }
 
 }  // namespace
+
+ssm_status plan_footprint(const ssm_params& p, bool staging, int64_t* persistent, int64_t* peak) {
+  return footprint_impl(p, staging, persistent, peak);
+}
+
+ssm_status validate_params(const ssm_params* p) { return validate(p); }
+
 }  // namespace ssm
 
 using namespace ssm;
@@ -550,27 +749,15 @@ ssm_status ssm_solve_host(ssm_plan_t plan, const float* M_host, int64_t ldm, flo
   SSM_CUDA(cudaSetDevice(plan->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t ld = plan->g.ld;
-  if (!plan->Mstage) SSM_TRY(dalloc(&plan->Mstage, (size_t)plan->P * ld, s));
-  if (!plan->Fstage) SSM_TRY(dalloc(&plan->Fstage, (size_t)plan->Q * ld, s));
+  if (!plan->Mstage) SSM_TRY(palloc(plan, &plan->Mstage, (size_t)plan->P * ld, s));
+  if (!plan->Fstage) SSM_TRY(palloc(plan, &plan->Fstage, (size_t)plan->Q * ld, s));
   SSM_CUDA(cudaMemcpy2DAsync(plan->Mstage, sizeof(float) * ld, M_host, sizeof(float) * ldm,
                              sizeof(float) * plan->g.N, plan->P, cudaMemcpyHostToDevice, s));
-  ssm_status st = solve_impl(plan, plan->Mstage, ld, plan->Fstage, ld, nullptr, s);
+  ssm_status st = solve_impl(plan, plan->Mstage, ld, plan->Fstage, ld, info, s);
   if (st != SSM_OK && st != SSM_ENOTCONVERGED) return st;
   SSM_CUDA(cudaMemcpy2DAsync(F_host, sizeof(float) * ldf, plan->Fstage, sizeof(float) * ld,
                              sizeof(float) * plan->g.N, plan->Q, cudaMemcpyDeviceToHost, s));
   SSM_CUDA(cudaStreamSynchronize(s));
-  if (info) {
-    // the device-side info of the last solve is not kept; recompute the cheap fields
-    info->status = st;
-    info->rank = plan->r;
-    info->gram_side = plan->gram_side;
-    info->xi_p = plan->xi;
-    info->dtd_norm = plan->dtd_norm;
-    info->sigma1 = plan->sigma1;
-    info->plan_ms = plan->plan_ms;
-    info->iterations = -1;
-    info->res_primal = info->res_change = -1;
-  }
   return st;
 }
 
@@ -587,7 +774,7 @@ ssm_status ssm_objective(ssm_plan_t plan, const float* M_dev, int64_t ldm, const
   SSM_CUDA(cudaSetDevice(plan->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t ld = plan->g.ld;
-  if (!plan->Res) SSM_TRY(dalloc(&plan->Res, (size_t)plan->P * ld, s));
+  if (!plan->Res) SSM_TRY(palloc(plan, &plan->Res, (size_t)plan->P * ld, s));
   SSM_CUDA(cudaMemcpy2DAsync(plan->Res, sizeof(float) * ld, M_dev, sizeof(float) * ldm,
                              sizeof(float) * plan->g.N, plan->P, cudaMemcpyDeviceToDevice, s));
   const float* Kd = (use_full_k || plan->p.form == SSM_FORM_DENSE) ? plan->K32 : plan->Kr32;
@@ -625,6 +812,35 @@ ssm_status ssm_plan_factors(ssm_plan_t plan, double* sigma_host, double* vr_host
         vr_host[(size_t)q * plan->r + i] = v;
       }
   }
+  return SSM_OK;
+}
+
+ssm_status ssm_plan_set_graphs(ssm_plan_t plan, int enable) {
+  if (!plan) {
+    set_error("NULL plan");
+    return SSM_EINVAL;
+  }
+  plan->use_graphs = enable != 0;
+  return SSM_OK;
+}
+
+ssm_status ssm_plan_footprint(const ssm_params* p, int device, int64_t* persistent_bytes,
+                              int64_t* peak_bytes) {
+  SSM_TRY(validate(p));
+  if (!persistent_bytes || !peak_bytes) {
+    set_error("NULL output");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(device));
+  return footprint_impl(*p, true, persistent_bytes, peak_bytes);
+}
+
+ssm_status ssm_plan_device_bytes(ssm_plan_t plan, int64_t* bytes) {
+  if (!plan || !bytes) {
+    set_error("NULL argument");
+    return SSM_EINVAL;
+  }
+  *bytes = plan->bytes;
   return SSM_OK;
 }
 
@@ -674,6 +890,7 @@ const char* ssm_status_string(int status) {
     case SSM_ETIMEOUT: return "device wait timed out";
     case SSM_EUNSUPPORTED: return "unsupported configuration";
     case SSM_ENOTCONVERGED: return "tolerance not reached within max_iter";
+    case SSM_EPENDING: return "request not finished";
     default: return "unknown status";
   }
 }

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -19,6 +20,13 @@ namespace ssm {
 // ------------------------------------------------------------------------------------
 void set_error(const std::string& msg);
 extern std::atomic<int64_t> g_launches;
+// kernels launched (or captured into a graph) by the calling thread
+extern thread_local int64_t t_launches;
+
+// SM count of the current device (queried once per device; safe from any thread)
+int sm_count();
+// serialises the one-time kernel attribute / occupancy set-up across host threads
+std::mutex& attr_mutex();
 
 #define SSM_CUDA(call)                                                                   \
   do {                                                                                   \
@@ -32,6 +40,7 @@ extern std::atomic<int64_t> g_launches;
 #define SSM_LAUNCHED()                                                                   \
   do {                                                                                   \
     ::ssm::g_launches.fetch_add(1, std::memory_order_relaxed);                           \
+    ++::ssm::t_launches;                                                                 \
     cudaError_t e_ = cudaGetLastError();                                                 \
     if (e_ != cudaSuccess) {                                                             \
       ::ssm::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));         \
@@ -56,6 +65,15 @@ struct Grid {
 
 // the largest padded rank the fused low-rank kernel is instantiated for
 constexpr int kMaxRank = 64;
+
+// a block of iterations captured once and replayed as a CUDA graph; `key` holds the
+// start parity, the block length and each iteration's (test, next test) flags
+struct GraphBlock {
+  std::string key;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;   // kernel launches one replay performs
+  int nparts = 0;        // residual partial rows written by the block's last iteration
+};
 
 // ------------------------------------------------------------------------------------
 // the plan (opaque ssm_plan_t)
@@ -119,9 +137,18 @@ struct ssm_plan_s {
   bool prof_enabled = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)
   size_t prof_used = 0;              // pairs recorded since the last read
+  // device bytes the plan holds (every allocation it owns)
+  int64_t bytes = 0;
+  // iteration blocks replayed as CUDA graphs (ssm_plan_set_graphs)
+  bool use_graphs = false;
+  std::vector<ssm::GraphBlock> graphs;
 };
 
 namespace ssm {
+
+// parameter checks of ssm_plan; device bytes of a plan for p (see ssm_plan_footprint)
+ssm_status validate_params(const ssm_params* p);
+ssm_status plan_footprint(const ssm_params& p, bool staging, int64_t* persistent, int64_t* peak);
 
 // ------------------------------------------------------------------------------------
 // launchers (each returns a status; the stream is the caller's)

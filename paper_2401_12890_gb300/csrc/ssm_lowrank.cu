@@ -328,7 +328,6 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
   }
 }
 
-int g_nsm = 0;
 
 template <int R>
 size_t smem_for(int nr) { return (size_t)Layout(R, nr).total + 128; }
@@ -348,19 +347,23 @@ ssm_status launch_r(const LowrankMaps& maps, const LowrankArgs& args, bool check
 // resident CTAs per SM for rank R (registers and shared memory), set up once per R
 template <int R>
 int blocks_per_sm(int nr) {
-  static int cached[5] = {0, 0, 0, 0, 0};
-  if (cached[nr] == 0) {
-    const size_t shm = smem_for<R>(nr);
-    cudaFuncSetAttribute(lowrank_iter_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)shm);
-    cudaFuncSetAttribute(lowrank_iter_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)shm);
-    int b1 = 0, b2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, lowrank_iter_kernel<R, true>, NT, shm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, lowrank_iter_kernel<R, false>, NT, shm);
-    cached[nr] = std::max(1, std::min(b1, b2));
-  }
-  return cached[nr];
+  static std::atomic<int> cached[5];
+  int v = cached[nr].load(std::memory_order_acquire);
+  if (v != 0) return v;
+  std::lock_guard<std::mutex> lock(attr_mutex());
+  v = cached[nr].load(std::memory_order_relaxed);
+  if (v != 0) return v;
+  const size_t shm = smem_for<R>(nr);
+  cudaFuncSetAttribute(lowrank_iter_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)shm);
+  cudaFuncSetAttribute(lowrank_iter_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)shm);
+  int b1 = 0, b2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, lowrank_iter_kernel<R, true>, NT, shm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, lowrank_iter_kernel<R, false>, NT, shm);
+  v = std::max(1, std::min(b1, b2));
+  cached[nr].store(v, std::memory_order_release);
+  return v;
 }
 
 // tensor maps of the current ping-pong state (encoding is a ~1 us host computation)
@@ -392,16 +395,10 @@ int bpsm_for(int R, int nr) {
 
 // persistent grid: every resident slot, but at least two stages of rows per CTA
 int64_t lowrank_grid(const ssm_plan_s* pl) {
-  if (g_nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (g_nsm <= 0) g_nsm = 148;
-  }
   const int nr = (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 ? 2 : 0);
   const int64_t ntiles = (pl->g.N + TV - 1) / TV;
   const int64_t T = ntiles * pl->Q;
-  int64_t grid = (int64_t)g_nsm * bpsm_for(pl->R, nr);
+  int64_t grid = (int64_t)sm_count() * bpsm_for(pl->R, nr);
   if (const char* env = getenv("SSM_LOWRANK_GRID")) {   // launch-shape override for sweeps
     const long v = atol(env);
     if (v >= 1 && v <= 65536) grid = v;

@@ -1,0 +1,492 @@
+// Continuous-batching server (ssm_server_* in include/ssm.h).
+//
+// Requests wait in a first-come first-served queue. A free worker (a host thread with
+// its own non-blocking CUDA stream) admits the first queued request whose device
+// footprint fits in the HBM budget; a later request may pass the head of the queue
+// when the head does not fit yet, at most `max_bypass` times per head. Admitted
+// solves run concurrently on their streams, so kernels of different solves overlap on
+// the GPU. Plans stay resident after their solve (when plan caching is on) and are
+// reused by a later request with the same dictionary, grid and plan parameters; idle
+// plans are evicted least recently used first when a request needs their memory.
+//
+// Memory accounting: every plan (running or idle) has a reservation, its peak
+// footprint while planning and its persistent footprint afterwards. `held` sums the
+// reservations of live plans, `dying` those of evicted plans not yet freed. A worker
+// that evicts plans to admit a request frees them before it plans, so the device
+// memory the plans hold never exceeds the budget, and held never exceeds it either.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+
+#include "ssm_internal.cuh"
+
+namespace ssm {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+// parameters that determine a plan (everything but the stopping rule), normalised so
+// that equivalent settings compare equal
+bool same_plan(const ssm_params& a, const ssm_params& b) {
+  if (a.ndim != b.ndim || a.P != b.P || a.Q != b.Q) return false;
+  for (int d = 0; d < a.ndim; ++d)
+    if (a.dims[d] != b.dims[d]) return false;
+  const double xa = a.xi_p > 0 ? a.xi_p : 0.0, xb = b.xi_p > 0 ? b.xi_p : 0.0;
+  const double ta = a.rank_tol > 0 ? a.rank_tol : 5e-5, tb = b.rank_tol > 0 ? b.rank_tol : 5e-5;
+  const int pa = a.form == SSM_FORM_DENSE ? a.precision : 0;
+  const int pb = b.form == SSM_FORM_DENSE ? b.precision : 0;
+  const int ra = a.form == SSM_FORM_LOWRANK ? a.rank : 0;
+  const int rb = b.form == SSM_FORM_LOWRANK ? b.rank : 0;
+  return a.lambda == b.lambda && a.beta == b.beta && xa == xb && a.form == b.form && ra == rb &&
+         (a.form != SSM_FORM_LOWRANK || a.rank > 0 || ta == tb) && pa == pb &&
+         a.stencil_pairs == b.stencil_pairs;
+}
+
+// FNV-1a style hash over the dictionary, one double at a time (a filter only: a match
+// is confirmed byte by byte)
+uint64_t hash_doubles(const double* data, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t w;
+    std::memcpy(&w, data + i, sizeof(w));
+    h ^= w;
+    h *= 1099511628211ull;
+    h ^= h >> 29;
+  }
+  return h;
+}
+
+struct Resident {
+  ssm_plan_t plan = nullptr;
+  ssm_params p{};
+  std::vector<double> K;     // the dictionary the plan was made from
+  uint64_t khash = 0;
+  int64_t bytes = 0;         // reservation
+  bool busy = false;
+  uint64_t last_used = 0;
+};
+
+struct Request {
+  int64_t ticket = 0;
+  ssm_params p{};
+  const double* K = nullptr;
+  const float* M = nullptr;
+  int64_t ldm = 0;
+  float* F = nullptr;
+  int64_t ldf = 0;
+  uint64_t khash = 0;
+  int64_t footprint = 0;     // peak estimate (reserved at admission)
+  int bypassed = 0;
+  bool done = false;
+  Clock::time_point t_submit, t_admit, t_done;
+  ssm_request_info info{};
+  std::string error;
+};
+
+}  // namespace
+}  // namespace ssm
+
+using namespace ssm;
+
+struct ssm_server_s {
+  ssm_server_config cfg{};
+  int64_t budget = 0;
+  std::mutex mu;
+  std::condition_variable cv_work;   // queue changed, memory freed, or stop
+  std::condition_variable cv_done;   // a request finished
+  std::deque<Request*> pending;
+  std::unordered_map<int64_t, std::unique_ptr<Request>> requests;
+  std::list<std::unique_ptr<Resident>> residents;
+  int64_t held = 0, dying = 0, peak = 0;
+  int64_t next_ticket = 1, next_order = 0;
+  uint64_t tick = 0;
+  int active = 0;
+  bool stop = false;
+  ssm_server_stats st{};
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;
+
+  // choose a request to run (caller holds mu); fills the plan to use and the idle
+  // plans to free first
+  bool try_admit(Request** out, Resident** res_out, std::vector<std::unique_ptr<Resident>>* evict) {
+    for (size_t i = 0; i < pending.size(); ++i) {
+      Request* q = pending[i];
+      Resident* match = nullptr;
+      if (cfg.cache_plans)
+        for (auto& r : residents)
+          if (!r->busy && r->khash == q->khash && same_plan(r->p, q->p) &&
+              r->K.size() == (size_t)q->p.P * q->p.Q &&
+              std::memcmp(r->K.data(), q->K, sizeof(double) * r->K.size()) == 0) {
+            match = r.get();
+            break;
+          }
+      const int64_t need = match ? 0 : q->footprint;
+      int64_t avail = budget - held - dying;
+      std::vector<Resident*> picks;
+      if (need > avail) {
+        std::vector<Resident*> idle;
+        for (auto& r : residents)
+          if (!r->busy && r.get() != match) idle.push_back(r.get());
+        std::sort(idle.begin(), idle.end(),
+                  [](const Resident* a, const Resident* b) { return a->last_used < b->last_used; });
+        for (Resident* r : idle) {
+          if (need <= avail) break;
+          picks.push_back(r);
+          avail += r->bytes;
+        }
+      }
+      if (need <= avail) {
+        for (Resident* r : picks) {
+          for (auto it = residents.begin(); it != residents.end(); ++it)
+            if (it->get() == r) {
+              held -= r->bytes;
+              dying += r->bytes;
+              evict->push_back(std::move(*it));
+              residents.erase(it);
+              break;
+            }
+          ++st.plans_evicted;
+        }
+        if (match) {
+          match->busy = true;
+          *res_out = match;
+          q->info.plan_reused = 1;
+          ++st.plans_reused;
+        } else {
+          auto r = std::make_unique<Resident>();
+          r->p = q->p;
+          r->khash = q->khash;
+          r->bytes = need;
+          r->busy = true;
+          held += need;
+          *res_out = r.get();
+          residents.push_back(std::move(r));
+        }
+        peak = std::max(peak, held);
+        pending.erase(pending.begin() + (std::ptrdiff_t)i);
+        if (i > 0) ++pending.front()->bypassed;
+        *out = q;
+        return true;
+      }
+      if (i == 0 && q->bypassed >= cfg.max_bypass) return false;
+    }
+    return false;
+  }
+
+  // run one admitted request on `slot`'s stream; returns the solve's status
+  ssm_status run(Request* q, Resident* res, int slot) {
+    const bool sim = cfg.simulate_us > 0;
+    if (!res->plan && !sim) {
+      const Clock::time_point t0 = Clock::now();
+      res->K.assign(q->K, q->K + (size_t)q->p.P * q->p.Q);
+      SSM_TRY(ssm_plan(&res->plan, &q->p, q->K, cfg.device, streams[slot]));
+      q->info.plan_ms = ms_between(t0, Clock::now());
+      if (cfg.use_graphs) ssm_plan_set_graphs(res->plan, 1);
+      // planning's temporaries are gone: keep only the persistent reservation
+      ssm_params pr = q->p;
+      if (pr.form == SSM_FORM_LOWRANK) pr.rank = res->plan->r;
+      int64_t persistent = 0, peak_b = 0;
+      if (plan_footprint(pr, true, &persistent, &peak_b) == SSM_OK && persistent < res->bytes) {
+        std::lock_guard<std::mutex> lk(mu);
+        held -= res->bytes - persistent;
+        res->bytes = persistent;
+      }
+    } else if (sim && res->K.empty()) {
+      res->K.assign(q->K, q->K + (size_t)q->p.P * q->p.Q);
+    }
+    if (sim) {
+      std::this_thread::sleep_for(
+          std::chrono::microseconds((int64_t)q->p.max_iter * cfg.simulate_us));
+      q->info.iterations = 0;
+      q->info.res_primal = q->info.res_change = -1;
+      return SSM_OK;
+    }
+    // the stopping rule is per request
+    res->plan->p.max_iter = q->p.max_iter;
+    res->plan->p.check_every = q->p.check_every;
+    res->plan->p.tol_primal = q->p.tol_primal;
+    res->plan->p.tol_change = q->p.tol_change;
+    ssm_info inf{};
+    const ssm_status s =
+        ssm_solve_host(res->plan, q->M, q->ldm, q->F, q->ldf, &inf, streams[slot]);
+    q->info.iterations = inf.iterations;
+    q->info.res_primal = inf.res_primal;
+    q->info.res_change = inf.res_change;
+    return s;
+  }
+
+  void worker(int slot) {
+    const bool sim = cfg.simulate_us > 0;
+    if (!sim) cudaSetDevice(cfg.device);
+    for (;;) {
+      Request* q = nullptr;
+      Resident* res = nullptr;
+      std::vector<std::unique_ptr<Resident>> evict;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_work.wait(lk, [&] { return stop || (!pending.empty() && try_admit(&q, &res, &evict)); });
+        if (!q) return;   // stop
+        ++active;
+        q->t_admit = Clock::now();
+        q->info.order = next_order++;
+        q->info.slot = slot;
+      }
+      if (!evict.empty()) {
+        int64_t freed = 0;
+        for (auto& r : evict) {
+          if (r->plan) ssm_destroy(r->plan);
+          freed += r->bytes;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        dying -= freed;
+      }
+      const ssm_status s = run(q, res, slot);
+      const std::string err = s == SSM_OK || s == SSM_ENOTCONVERGED ? "" : ssm_last_error();
+      std::unique_ptr<Resident> drop;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        q->t_done = Clock::now();
+        q->info.status = s;
+        q->info.queue_ms = ms_between(q->t_submit, q->t_admit);
+        q->info.solve_ms = ms_between(q->t_admit, q->t_done);
+        q->info.latency_ms = ms_between(q->t_submit, q->t_done);
+        q->error = err;
+        q->done = true;
+        res->busy = false;
+        res->last_used = ++tick;
+        const bool bad = s != SSM_OK && s != SSM_ENOTCONVERGED;
+        if (!q->info.plan_reused && (res->plan || sim) && !bad) ++st.plans_created;
+        if (bad) ++st.failed;
+        else ++st.completed;
+        // a plan that failed to build, or any plan when caching is off, is freed now
+        if (!cfg.cache_plans || (!res->plan && !sim) || bad) {
+          for (auto it = residents.begin(); it != residents.end(); ++it)
+            if (it->get() == res) {
+              held -= res->bytes;
+              dying += res->bytes;
+              drop = std::move(*it);
+              residents.erase(it);
+              break;
+            }
+        }
+        --active;
+      }
+      if (drop) {
+        if (drop->plan) ssm_destroy(drop->plan);
+        std::lock_guard<std::mutex> lk(mu);
+        dying -= drop->bytes;
+      }
+      cv_done.notify_all();
+      cv_work.notify_all();
+    }
+  }
+};
+
+namespace {
+
+ssm_status collect(ssm_server_s* s, std::unique_lock<std::mutex>& lk, int64_t ticket,
+                   ssm_request_info* info) {
+  auto it = s->requests.find(ticket);
+  (void)lk;
+  if (it == s->requests.end()) {
+    set_error("unknown ticket");
+    return SSM_EINVAL;
+  }
+  if (!it->second->done) return SSM_EPENDING;
+  if (info) *info = it->second->info;
+  if (!it->second->error.empty()) set_error(it->second->error);
+  s->requests.erase(it);
+  return SSM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ssm_status ssm_server_default_config(ssm_server_config* c) {
+  if (!c) return SSM_EINVAL;
+  std::memset(c, 0, sizeof(*c));
+  c->device = 0;
+  c->max_active = 4;
+  c->hbm_budget = 0;
+  c->use_graphs = 1;
+  c->cache_plans = 1;
+  c->max_bypass = -1;
+  c->simulate_us = 0;
+  return SSM_OK;
+}
+
+ssm_status ssm_server_create(ssm_server_t* out, const ssm_server_config* c) {
+  if (!out || !c) {
+    set_error("NULL argument");
+    return SSM_EINVAL;
+  }
+  *out = nullptr;
+  if (c->max_active < 1 || c->max_active > 256) {
+    set_error("max_active must be in [1, 256]");
+    return SSM_EINVAL;
+  }
+  auto s = std::make_unique<ssm_server_s>();
+  s->cfg = *c;
+  if (s->cfg.max_bypass < 0) s->cfg.max_bypass = 2 * c->max_active;
+  const bool sim = c->simulate_us > 0;
+  if (sim) {
+    if (c->hbm_budget <= 0) {
+      set_error("scheduler test mode needs an explicit hbm_budget");
+      return SSM_EINVAL;
+    }
+    s->budget = c->hbm_budget;
+  } else {
+    int prev = 0;
+    SSM_CUDA(cudaGetDevice(&prev));
+    SSM_CUDA(cudaSetDevice(c->device));
+    size_t free_b = 0, total_b = 0;
+    const cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e == cudaSuccess) {
+      s->budget = c->hbm_budget > 0 ? std::min<int64_t>(c->hbm_budget, (int64_t)free_b)
+                                    : (int64_t)(0.9 * (double)free_b);
+      s->streams.resize(c->max_active);
+      for (auto& st : s->streams) {
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+          set_error("cudaStreamCreateWithFlags failed");
+          for (auto& x : s->streams)
+            if (x) cudaStreamDestroy(x);
+          cudaSetDevice(prev);
+          return SSM_ECUDA;
+        }
+      }
+    }
+    cudaSetDevice(prev);
+    SSM_CUDA(e);
+  }
+  s->st.budget = s->budget;
+  ssm_server_s* raw = s.get();
+  for (int i = 0; i < c->max_active; ++i) raw->workers.emplace_back([raw, i] { raw->worker(i); });
+  *out = s.release();
+  return SSM_OK;
+}
+
+ssm_status ssm_server_submit(ssm_server_t s, const ssm_params* p, const double* K_host,
+                             const float* M_host, int64_t ldm, float* F_host, int64_t ldf,
+                             int64_t* ticket) {
+  if (!s || !ticket || !K_host || !M_host || !F_host) {
+    set_error("NULL argument");
+    return SSM_EINVAL;
+  }
+  SSM_TRY(validate_params(p));
+  int64_t N = 1;
+  for (int d = 0; d < p->ndim; ++d) N *= p->dims[d];
+  if (ldm < N || ldf < N) {
+    set_error("leading dimension smaller than N");
+    return SSM_EINVAL;
+  }
+  auto q = std::make_unique<Request>();
+  q->p = *p;
+  q->K = K_host;
+  q->M = M_host;
+  q->ldm = ldm;
+  q->F = F_host;
+  q->ldf = ldf;
+  q->khash = hash_doubles(K_host, (size_t)p->P * p->Q);
+  int64_t persistent = 0;
+  if (s->cfg.simulate_us > 0) {
+    SSM_TRY(plan_footprint(*p, true, &persistent, &q->footprint));
+    cudaGetLastError();   // device queries made without a device leave a sticky error
+  } else {
+    int prev = 0;
+    SSM_CUDA(cudaGetDevice(&prev));
+    SSM_CUDA(cudaSetDevice(s->cfg.device));
+    const ssm_status fs = plan_footprint(*p, true, &persistent, &q->footprint);
+    cudaSetDevice(prev);
+    SSM_TRY(fs);
+  }
+  q->info.footprint = q->footprint;
+  std::lock_guard<std::mutex> lk(s->mu);
+  ++s->st.submitted;
+  if (q->footprint > s->budget) {
+    ++s->st.rejected;
+    set_error("request footprint (" + std::to_string(q->footprint) +
+              " bytes) exceeds the server's HBM budget (" + std::to_string(s->budget) + ")");
+    return SSM_ENOMEM;
+  }
+  q->ticket = s->next_ticket++;
+  q->t_submit = Clock::now();
+  *ticket = q->ticket;
+  s->pending.push_back(q.get());
+  s->requests[q->ticket] = std::move(q);
+  s->cv_work.notify_all();
+  return SSM_OK;
+}
+
+ssm_status ssm_server_poll(ssm_server_t s, int64_t ticket, ssm_request_info* info) {
+  if (!s) {
+    set_error("NULL server");
+    return SSM_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(s->mu);
+  return collect(s, lk, ticket, info);
+}
+
+ssm_status ssm_server_wait(ssm_server_t s, int64_t ticket, double timeout_ms,
+                           ssm_request_info* info) {
+  if (!s) {
+    set_error("NULL server");
+    return SSM_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto ready = [&] {
+    auto it = s->requests.find(ticket);
+    return it == s->requests.end() || it->second->done;
+  };
+  if (timeout_ms < 0)
+    s->cv_done.wait(lk, ready);
+  else
+    s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), ready);
+  return collect(s, lk, ticket, info);
+}
+
+ssm_status ssm_server_stats_read(ssm_server_t s, ssm_server_stats* out) {
+  if (!s || !out) {
+    set_error("NULL argument");
+    return SSM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->st;
+  out->bytes_held = s->held;
+  out->peak_bytes_held = s->peak;
+  out->budget = s->budget;
+  out->active = s->active;
+  out->pending = (int)s->pending.size();
+  return SSM_OK;
+}
+
+ssm_status ssm_server_destroy(ssm_server_t s) {
+  if (!s) return SSM_OK;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.wait(lk, [&] { return s->pending.empty() && s->active == 0; });
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  const bool sim = s->cfg.simulate_us > 0;
+  if (!sim) cudaSetDevice(s->cfg.device);
+  for (auto& r : s->residents)
+    if (r->plan) ssm_destroy(r->plan);
+  for (auto& st : s->streams)
+    if (st) cudaStreamDestroy(st);
+  delete s;
+  return SSM_OK;
+}
+
+}  // extern "C"

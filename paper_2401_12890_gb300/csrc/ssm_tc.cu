@@ -253,22 +253,10 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
   }
 }
 
-int g_nsm_tc = 0;
-
-int nsm() {
-  if (g_nsm_tc == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_nsm_tc, cudaDevAttrMultiProcessorCount, dev);
-    if (g_nsm_tc <= 0) g_nsm_tc = 148;
-  }
-  return g_nsm_tc;
-}
-
 int gemm_grid(const ssm_plan_s* pl) {
   const int ntv = (int)((pl->g.N + BM - 1) / BM);
   const int ntq = (pl->Q + BN - 1) / BN;
-  return std::max(1, std::min(nsm(), ntv * ntq));
+  return std::max(1, std::min(sm_count(), ntv * ntq));
 }
 
 }  // namespace

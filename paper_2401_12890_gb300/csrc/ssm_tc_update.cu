@@ -224,34 +224,32 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
   }
 }
 
-int g_nsm_upd = 0;
-
-int nsm() {
-  if (g_nsm_upd == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_nsm_upd, cudaDevAttrMultiProcessorCount, dev);
-    if (g_nsm_upd <= 0) g_nsm_upd = 148;
-  }
-  return g_nsm_upd;
-}
-
 int update_nr(const ssm_plan_s* pl) { return (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 ? 2 : 0); }
 
 int update_grid_impl(const ssm_plan_s* pl) {
-  static int per_sm = 0;
+  // resident CTAs per SM, per number of halo rows (the shared-memory layout differs)
+  static std::atomic<int> cached[5];
+  const int nr = update_nr(pl);
+  int per_sm = cached[nr].load(std::memory_order_acquire);
   if (per_sm == 0) {
-    const size_t shm = (size_t)ULayout(4).total + 128;
-    cudaFuncSetAttribute(tc_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    cudaFuncSetAttribute(tc_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_update_kernel<true>, UNT,
-                                                  (size_t)ULayout(update_nr(pl)).total + 128);
-    per_sm = std::max(1, b);
+    std::lock_guard<std::mutex> lock(attr_mutex());
+    per_sm = cached[nr].load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+      const size_t shm = (size_t)ULayout(4).total + 128;
+      cudaFuncSetAttribute(tc_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)shm);
+      cudaFuncSetAttribute(tc_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)shm);
+      int b = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_update_kernel<true>, UNT,
+                                                    (size_t)ULayout(nr).total + 128);
+      per_sm = std::max(1, b);
+      cached[nr].store(per_sm, std::memory_order_release);
+    }
   }
   const int64_t ntiles = (pl->g.N + UTV - 1) / UTV;
   const int64_t T = ntiles * ((pl->Q + UQC - 1) / UQC);
-  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm() * per_sm, T));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm, T));
 }
 
 }  // namespace

@@ -22,7 +22,7 @@ LIB_PATH = os.environ.get("SSM_LIBRARY", os.path.join(HERE, "libssm.so"))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ssm.h")
 
 SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENAN, SSM_ETIMEOUT, SSM_EUNSUPPORTED, \
-    SSM_ENOTCONVERGED = range(8)
+    SSM_ENOTCONVERGED, SSM_EPENDING = range(9)
 FORMS = {"lowrank": 0, "dense": 1}
 PRECISIONS = {"fp32": 0, "bf16x3": 1}
 
@@ -45,6 +45,41 @@ class SsmInfo(ctypes.Structure):
         ("gram_side", ctypes.c_int), ("xi_p", ctypes.c_double), ("dtd_norm", ctypes.c_double),
         ("sigma1", ctypes.c_double), ("res_primal", ctypes.c_double),
         ("res_change", ctypes.c_double), ("plan_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SsmServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int), ("max_active", ctypes.c_int), ("hbm_budget", ctypes.c_int64),
+        ("use_graphs", ctypes.c_int), ("cache_plans", ctypes.c_int),
+        ("max_bypass", ctypes.c_int), ("simulate_us", ctypes.c_int64),
+    ]
+
+
+class SsmRequestInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("iterations", ctypes.c_int),
+        ("res_primal", ctypes.c_double), ("res_change", ctypes.c_double),
+        ("queue_ms", ctypes.c_double), ("plan_ms", ctypes.c_double),
+        ("solve_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+        ("footprint", ctypes.c_int64), ("order", ctypes.c_int64), ("slot", ctypes.c_int),
+        ("plan_reused", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SsmServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+        ("rejected", ctypes.c_int64), ("plans_created", ctypes.c_int64),
+        ("plans_reused", ctypes.c_int64), ("plans_evicted", ctypes.c_int64),
+        ("bytes_held", ctypes.c_int64), ("peak_bytes_held", ctypes.c_int64),
+        ("budget", ctypes.c_int64), ("active", ctypes.c_int), ("pending", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -92,13 +127,28 @@ def load_library(path: str = LIB_PATH):
                                           ctypes.c_double, ctypes.c_int, dp, vp]
     lib.ssm_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.ssm_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
+    lib.ssm_plan_set_graphs.argtypes = [vp, ctypes.c_int]
+    lib.ssm_plan_footprint.argtypes = [ctypes.POINTER(SsmParams), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.ssm_plan_device_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.ssm_server_default_config.argtypes = [ctypes.POINTER(SsmServerConfig)]
+    lib.ssm_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SsmServerConfig)]
+    lib.ssm_server_submit.argtypes = [vp, ctypes.POINTER(SsmParams), vp, vp, i64, vp, i64,
+                                      ctypes.POINTER(ctypes.c_int64)]
+    lib.ssm_server_poll.argtypes = [vp, i64, ctypes.POINTER(SsmRequestInfo)]
+    lib.ssm_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(SsmRequestInfo)]
+    lib.ssm_server_stats_read.argtypes = [vp, ctypes.POINTER(SsmServerStats)]
+    lib.ssm_server_destroy.argtypes = [vp]
     lib.ssm_status_string.argtypes = [ctypes.c_int]
     lib.ssm_status_string.restype = ctypes.c_char_p
     lib.ssm_last_error.restype = ctypes.c_char_p
     lib.ssm_launch_count.restype = ctypes.c_int64
     for name in ("ssm_default_params", "ssm_plan", "ssm_solve", "ssm_solve_host",
                  "ssm_objective", "ssm_plan_factors", "ssm_destroy", "ssm_profile_enable",
-                 "ssm_profile_read", "ssm_objective_noalloc"):
+                 "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
+                 "ssm_plan_footprint", "ssm_plan_device_bytes", "ssm_server_default_config",
+                 "ssm_server_create", "ssm_server_submit", "ssm_server_poll", "ssm_server_wait",
+                 "ssm_server_stats_read", "ssm_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -117,6 +167,39 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def make_params(P, Q, dims, lam, beta, *, form="lowrank", precision="fp32", rank=0,
+                rank_tol=5e-5, xi_p=0.0, stencil_pairs=2, max_iter=300, check_every=10,
+                tol_primal=0.0, tol_change=0.0) -> SsmParams:
+    """ssm_params for a P x Q dictionary on the grid `dims`."""
+    lib = load_library()
+    p = SsmParams()
+    lib.ssm_default_params(ctypes.byref(p))
+    dims = tuple(int(d) for d in dims)
+    p.ndim = len(dims)
+    for i, d in enumerate(dims):
+        p.dims[i] = d
+    p.P, p.Q = int(P), int(Q)
+    p.lam, p.beta, p.xi_p = float(lam), float(beta), float(xi_p)
+    p.form = FORMS[form]
+    p.precision = PRECISIONS[precision]
+    p.rank, p.rank_tol = int(rank), float(rank_tol)
+    p.stencil_pairs = int(stencil_pairs)
+    p.max_iter, p.check_every = int(max_iter), int(check_every)
+    p.tol_primal, p.tol_change = float(tol_primal), float(tol_change)
+    return p
+
+
+def footprint(P, Q, dims, *, device=0, **kw):
+    """(persistent, peak) device bytes of a plan (ssm_plan_footprint)."""
+    p = make_params(P, Q, dims, kw.pop("lam", 0.0), kw.pop("beta", 1.0), **kw)
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    st = load_library().ssm_plan_footprint(ctypes.byref(p), int(device), ctypes.byref(a),
+                                           ctypes.byref(b))
+    if st != SSM_OK:
+        raise SsmError(st, "ssm_plan_footprint")
+    return a.value, b.value
+
+
 class Plan:
     """A planned solver for one dictionary K (P x Q) and one voxel grid."""
 
@@ -125,20 +208,11 @@ class Plan:
                  tol_primal=0.0, tol_change=0.0, device=0, stream=None):
         lib = load_library()
         K = np.ascontiguousarray(K, dtype=np.float64)
-        p = SsmParams()
-        lib.ssm_default_params(ctypes.byref(p))
+        p = make_params(K.shape[0], K.shape[1], dims, lam, beta, form=form,
+                        precision=precision, rank=rank, rank_tol=rank_tol, xi_p=xi_p,
+                        stencil_pairs=stencil_pairs, max_iter=max_iter,
+                        check_every=check_every, tol_primal=tol_primal, tol_change=tol_change)
         dims = tuple(int(d) for d in dims)
-        p.ndim = len(dims)
-        for i, d in enumerate(dims):
-            p.dims[i] = d
-        p.P, p.Q = int(K.shape[0]), int(K.shape[1])
-        p.lam, p.beta, p.xi_p = float(lam), float(beta), float(xi_p)
-        p.form = FORMS[form]
-        p.precision = PRECISIONS[precision]
-        p.rank, p.rank_tol = int(rank), float(rank_tol)
-        p.stencil_pairs = int(stencil_pairs)
-        p.max_iter, p.check_every = int(max_iter), int(check_every)
-        p.tol_primal, p.tol_change = float(tol_primal), float(tol_change)
         self.params = p
         self.dims = dims
         self.P, self.Q = p.P, p.Q
@@ -149,6 +223,19 @@ class Plan:
                           K.ctypes.data_as(ctypes.c_void_p), int(device), _stream_handle(stream))
         if st != SSM_OK:
             raise SsmError(st, "ssm_plan")
+
+    def set_graphs(self, enable=True):
+        """Replay iteration blocks as CUDA graphs (ssm_plan_set_graphs)."""
+        st = load_library().ssm_plan_set_graphs(self._h, int(bool(enable)))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_plan_set_graphs")
+
+    def device_bytes(self):
+        b = ctypes.c_int64()
+        st = load_library().ssm_plan_device_bytes(self._h, ctypes.byref(b))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_plan_device_bytes")
+        return b.value
 
     def solve(self, M, out=None, stream=None):
         """M: CUDA float32 tensor P x N (row stride >= N). Returns (F tensor Q x N, info)."""
@@ -175,14 +262,18 @@ class Plan:
             raise SsmError(st, "ssm_solve")
         return st
 
-    def solve_host(self, M_host, F_host, stream=None):
-        """Host buffers (torch CPU tensors, pinned for async copies). Returns the status."""
+    def solve_host(self, M_host, F_host, stream=None, with_info=False):
+        """Host buffers (torch CPU tensors, pinned for async copies). Returns the status,
+        or (status, info) with `with_info`."""
+        info = SsmInfo()
         st = load_library().ssm_solve_host(self._h, ctypes.c_void_p(M_host.data_ptr()),
                                            M_host.stride(0), ctypes.c_void_p(F_host.data_ptr()),
-                                           F_host.stride(0), None, _stream_handle(stream))
+                                           F_host.stride(0),
+                                           ctypes.byref(info) if with_info else None,
+                                           _stream_handle(stream))
         if st not in (SSM_OK, SSM_ENOTCONVERGED):
             raise SsmError(st, "ssm_solve_host")
-        return st
+        return (st, info.as_dict()) if with_info else st
 
     def objective(self, M, F, use_full_k=False, stream=None):
         J = ctypes.c_double()
@@ -228,6 +319,93 @@ class Plan:
         if self._h:
             load_library().ssm_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (ssm_server_* in include/ssm.h).
+
+    submit() queues one solve on host arrays and returns a ticket; wait() returns
+    (F, info) when it has finished. The arrays are kept alive here until then.
+    """
+
+    def __init__(self, *, device=0, max_active=4, hbm_budget=0, use_graphs=True,
+                 cache_plans=True, max_bypass=-1, simulate_us=0):
+        lib = load_library()
+        c = SsmServerConfig()
+        lib.ssm_server_default_config(ctypes.byref(c))
+        c.device, c.max_active, c.hbm_budget = int(device), int(max_active), int(hbm_budget)
+        c.use_graphs, c.cache_plans = int(bool(use_graphs)), int(bool(cache_plans))
+        c.max_bypass, c.simulate_us = int(max_bypass), int(simulate_us)
+        self._h = ctypes.c_void_p()
+        st = lib.ssm_server_create(ctypes.byref(self._h), ctypes.byref(c))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_server_create")
+        self._keep = {}
+
+    def submit(self, K, M, dims, lam, beta, *, out=None, **kw):
+        """K: P x Q (float64), M: P x N host array (float32). Returns a ticket."""
+        K = np.ascontiguousarray(K, dtype=np.float64)
+        M = np.ascontiguousarray(M, dtype=np.float32)
+        P, Q = K.shape
+        N = int(np.prod(dims))
+        assert M.shape == (P, N)
+        F = out if out is not None else np.empty((Q, N), dtype=np.float32)
+        assert F.dtype == np.float32 and F.flags.c_contiguous and F.shape == (Q, N)
+        p = make_params(P, Q, dims, lam, beta, **kw)
+        t = ctypes.c_int64()
+        st = load_library().ssm_server_submit(
+            self._h, ctypes.byref(p), K.ctypes.data_as(ctypes.c_void_p),
+            M.ctypes.data_as(ctypes.c_void_p), N, F.ctypes.data_as(ctypes.c_void_p), N,
+            ctypes.byref(t))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_server_submit")
+        self._keep[t.value] = (K, M, F)
+        return t.value
+
+    def _finish(self, ticket, st, info):
+        if st == SSM_EPENDING:
+            return None
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_server_wait")
+        _, _, F = self._keep.pop(ticket)
+        return F, info.as_dict()
+
+    def wait(self, ticket, timeout_ms=-1.0):
+        """(F, info) of a finished request; None if the timeout ran out first."""
+        info = SsmRequestInfo()
+        st = load_library().ssm_server_wait(self._h, int(ticket), float(timeout_ms),
+                                            ctypes.byref(info))
+        return self._finish(ticket, st, info)
+
+    def poll(self, ticket):
+        info = SsmRequestInfo()
+        st = load_library().ssm_server_poll(self._h, int(ticket), ctypes.byref(info))
+        return self._finish(ticket, st, info)
+
+    def stats(self):
+        s = SsmServerStats()
+        st = load_library().ssm_server_stats_read(self._h, ctypes.byref(s))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_server_stats_read")
+        return s.as_dict()
+
+    def close(self):
+        if self._h:
+            load_library().ssm_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

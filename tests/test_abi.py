@@ -34,16 +34,22 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layout_matches_header(lib, tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ssm.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(ssm_params),'
-                   ' sizeof(ssm_info), offsetof(ssm_params, tol_change),'
-                   ' offsetof(ssm_info, plan_ms)); return 0;}\n')
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+                   ' sizeof(ssm_params), sizeof(ssm_info), offsetof(ssm_params, tol_change),'
+                   ' offsetof(ssm_info, plan_ms), sizeof(ssm_server_config),'
+                   ' offsetof(ssm_server_config, simulate_us), sizeof(ssm_request_info),'
+                   ' offsetof(ssm_request_info, plan_reused), sizeof(ssm_server_stats),'
+                   ' offsetof(ssm_server_stats, pending)); return 0;}\n')
     exe = tmp_path / "sz"
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                            check=True).stdout.split()]
     assert vals == [ctypes.sizeof(ssm.SsmParams), ctypes.sizeof(ssm.SsmInfo),
-                    ssm.SsmParams.tol_change.offset, ssm.SsmInfo.plan_ms.offset]
+                    ssm.SsmParams.tol_change.offset, ssm.SsmInfo.plan_ms.offset,
+                    ctypes.sizeof(ssm.SsmServerConfig), ssm.SsmServerConfig.simulate_us.offset,
+                    ctypes.sizeof(ssm.SsmRequestInfo), ssm.SsmRequestInfo.plan_reused.offset,
+                    ctypes.sizeof(ssm.SsmServerStats), ssm.SsmServerStats.pending.offset]
 
 
 def test_defaults_and_status_strings(lib):
@@ -51,7 +57,7 @@ def test_defaults_and_status_strings(lib):
     assert lib.ssm_default_params(ctypes.byref(p)) == ssm.SSM_OK
     assert p.ndim == 2 and p.beta == 1.0 and p.stencil_pairs == 2 and p.max_iter == 300
     assert p.rank_tol == pytest.approx(5e-5)
-    for code in range(8):
+    for code in range(9):
         assert lib.ssm_status_string(code)
     assert lib.ssm_status_string(99) == b"unknown status"
     assert lib.ssm_destroy(None) == ssm.SSM_OK

@@ -1,0 +1,196 @@
+"""Graph replay, plan footprints and the solve server on the GPU (needs a GB300).
+
+Bars, per test:
+  - graph replay gives results bitwise equal to direct launches of the same solve;
+  - a plan's device bytes equal the footprint estimate for its rank;
+  - a served solve gives the result of the same solve run alone, bitwise (the kernels
+    and their launch shapes do not depend on what else runs on the device), which is
+    stricter than the FP32 parity bar; served FP32 results also match the FP64 oracle
+    within 1e-5 (relative Frobenius) after their fixed iteration count.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ladmm as L
+from paper_2401_12890_gb300 import ssm, synth
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+    yield
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def solve_alone(K, M, dims, lam, beta, graphs=False, **kw):
+    """One solve through ssm_solve_host on a private stream; (F, info, kernels launched)."""
+    plan = ssm.Plan(K, dims, lam, beta, **kw)
+    if graphs:
+        plan.set_graphs(True)
+    stream = torch.cuda.Stream()
+    Mh = torch.from_numpy(np.ascontiguousarray(M, np.float32))
+    Fh = torch.empty((K.shape[1], Mh.shape[1]), dtype=torch.float32)
+    n0 = ssm.launch_count()
+    _, info = plan.solve_host(Mh, Fh, stream=stream, with_info=True)
+    launched = ssm.launch_count() - n0
+    out = [(Fh.numpy().copy(), info, launched)]
+    if graphs:          # a second solve replays the cached graphs
+        n0 = ssm.launch_count()
+        _, info2 = plan.solve_host(Mh, Fh, stream=stream, with_info=True)
+        out.append((Fh.numpy().copy(), info2, ssm.launch_count() - n0))
+    plan.close()
+    return out
+
+
+STOPS = [
+    dict(max_iter=130, check_every=0),                      # fixed budget, blocks of 64
+    dict(max_iter=37, check_every=10, tol_primal=1e-12),    # tests every 10, never met
+    dict(max_iter=400, check_every=7, tol_primal=2e-3),     # stops early on the test
+]
+FORMS = [dict(form="lowrank"), dict(form="dense"), dict(form="dense", precision="bf16x3")]
+
+
+@pytest.mark.parametrize("form", FORMS, ids=["lowrank", "dense_fp32", "dense_bf16x3"])
+@pytest.mark.parametrize("stop", STOPS, ids=["fixed", "tol_unmet", "tol_met"])
+def test_graph_replay_is_bitwise_equal_to_direct_launches(form, stop):
+    w = synth.WORKLOADS["dr2d_tiny"]
+    K, M, _ = synth.make_problem("dr2d_tiny", dims=(24, 20))
+    [(F0, i0, n0)] = solve_alone(K, M, (24, 20), w.lam, w.beta, **form, **stop)
+    (F1, i1, n1), (F2, i2, n2) = solve_alone(K, M, (24, 20), w.lam, w.beta, graphs=True,
+                                             **form, **stop)
+    assert np.array_equal(F0, F1) and np.array_equal(F0, F2)
+    for i in (i1, i2):
+        assert i["iterations"] == i0["iterations"]
+        assert i["res_primal"] == i0["res_primal"] and i["res_change"] == i0["res_change"]
+    assert n1 == n0 and n2 == n0          # the same kernels, counted at replay
+    if "tol_primal" in stop and stop["tol_primal"] > 1e-6:
+        assert i0["iterations"] < stop["max_iter"]
+
+
+@pytest.mark.parametrize("form", FORMS, ids=["lowrank", "dense_fp32", "dense_bf16x3"])
+def test_footprint_matches_plan_allocations(form):
+    w = synth.WORKLOADS["dr2d_tiny"]
+    K, M, _ = synth.make_problem("dr2d_tiny", dims=(40, 36))
+    plan = ssm.Plan(K, (40, 36), w.lam, w.beta, max_iter=3, **form)
+    Mh = torch.from_numpy(M)
+    Fh = torch.empty((K.shape[1], M.shape[1]), dtype=torch.float32)
+    plan.solve_host(Mh, Fh, stream=torch.cuda.Stream())   # allocates the host staging
+    held = plan.device_bytes()
+    r = plan.factors(with_vr=False)[2]
+    plan.close()
+    kw = dict(form)
+    if kw["form"] == "lowrank":
+        kw["rank"] = r
+    persistent, peak = ssm.footprint(K.shape[0], K.shape[1], (40, 36), lam=w.lam, beta=w.beta,
+                                     **kw)
+    assert persistent == held and peak > persistent
+    auto, _ = ssm.footprint(K.shape[0], K.shape[1], (40, 36), lam=w.lam, beta=w.beta, **form)
+    assert auto >= held
+
+
+def mixed_requests():
+    """Solves of differing grid, P, Q, form and stopping rule."""
+    reqs = []
+    w = synth.WORKLOADS["dr2d_tiny"]
+    K0, M0, _ = synth.make_problem("dr2d_tiny")
+    reqs.append(dict(K=K0, M=M0, dims=w.dims, lam=w.lam, beta=w.beta,
+                     kw=dict(form="lowrank", max_iter=300, check_every=0), oracle=True))
+    reqs.append(dict(K=K0, M=M0, dims=w.dims, lam=w.lam, beta=w.beta,
+                     kw=dict(form="dense", precision="bf16x3", max_iter=120, check_every=10,
+                             tol_primal=1e-3)))
+    K1, M1, _ = synth.random_problem(20, 48, (12, 10, 6), seed=5, snr=100)
+    reqs.append(dict(K=K1, M=M1, dims=(12, 10, 6), lam=0.05, beta=2.0,
+                     kw=dict(form="lowrank", max_iter=77, check_every=10, tol_primal=1e-9),
+                     oracle=True))
+    K2, M2, _ = synth.random_problem(64, 40, (40, 24), seed=6, snr=50, full_rank=True)
+    reqs.append(dict(K=K2, M=M2, dims=(40, 24), lam=0.01, beta=5.0,
+                     kw=dict(form="dense", max_iter=50, check_every=0), oracle=True))
+    K3, M3, _ = synth.random_problem(10, 30, (300,), seed=7, snr=100)
+    reqs.append(dict(K=K3, M=M3, dims=(300,), lam=0.1, beta=1.0,
+                     kw=dict(form="lowrank", rank=8, max_iter=33, check_every=0), oracle=True))
+    # the same dictionary and plan parameters as the first, other data: plan reuse
+    _, M0b, _ = synth.make_problem("dr2d_tiny", seed=99)
+    reqs.append(dict(K=K0, M=M0b, dims=w.dims, lam=w.lam, beta=w.beta,
+                     kw=dict(form="lowrank", max_iter=300, check_every=0)))
+    ws = synth.WORKLOADS["dr2d_slice"]
+    K4, M4, _ = synth.make_problem("dr2d_slice")
+    reqs.append(dict(K=K4, M=M4, dims=ws.dims, lam=ws.lam, beta=ws.beta,
+                     kw=dict(form="dense", precision="bf16x3", max_iter=30, check_every=0)))
+    reqs.append(dict(K=K4, M=M4, dims=ws.dims, lam=ws.lam, beta=ws.beta,
+                     kw=dict(form="lowrank", max_iter=40, check_every=10, tol_primal=1e-9)))
+    for r in reqs:
+        r["M"] = np.ascontiguousarray(r["M"], np.float32)
+    return reqs
+
+
+@pytest.fixture(scope="module")
+def alone():
+    reqs = mixed_requests()
+    for r in reqs:
+        [(F, info, _)] = solve_alone(r["K"], r["M"], r["dims"], r["lam"], r["beta"], **r["kw"])
+        r["F"], r["info"] = F, info
+    return reqs
+
+
+def serve_all(reqs, rounds=1, **server_kw):
+    out = []
+    with ssm.Server(**server_kw) as srv:
+        tickets = []
+        for _ in range(rounds):
+            for r in reqs:
+                tickets.append(srv.submit(r["K"], r["M"], r["dims"], r["lam"], r["beta"],
+                                          **r["kw"]))
+        for t in tickets:
+            out.append(srv.wait(t))
+        stats = srv.stats()
+    return out, stats
+
+
+def test_served_results_equal_solo_results(alone):
+    results, stats = serve_all(alone, rounds=2, max_active=3)
+    n = len(alone)
+    assert stats["completed"] == 2 * n and stats["failed"] == 0
+    assert stats["plans_reused"] >= 1
+    for k, (F, info) in enumerate(results):
+        r = alone[k % n]
+        assert info["status"] in (ssm.SSM_OK, ssm.SSM_ENOTCONVERGED)
+        assert info["iterations"] == r["info"]["iterations"]
+        diff = float(np.abs(F - r["F"]).max())
+        assert diff == 0.0, f"request {k}: served differs from solo by {diff:g}"
+        assert info["latency_ms"] >= info["solve_ms"] > 0
+
+
+def test_served_results_match_the_oracle(alone):
+    results, _ = serve_all(alone, max_active=4)
+    for r, (F, info) in zip(alone, results):
+        if not r.get("oracle"):
+            continue
+        kw = r["kw"]
+        ref = L.ladmm(r["K"], r["M"].astype(np.float64), r["dims"], r["lam"], r["beta"],
+                      dense=kw["form"] == "dense", rank=kw.get("rank") or None,
+                      iters=info["iterations"], check_every=0)
+        err = rel(F, ref["z"])
+        print(f"{kw['form']} {r['dims']}: rel err {err:.3e}")
+        assert err <= RTOL
+
+
+def test_tight_budget_serialises_and_evicts(alone):
+    _, peak1 = ssm.footprint(*alone[-1]["K"].shape, alone[-1]["dims"], lam=0.0, beta=1.0,
+                             form="dense", precision="bf16x3")
+    _, peak2 = ssm.footprint(*alone[-1]["K"].shape, alone[-1]["dims"], lam=0.0, beta=1.0,
+                             form="lowrank")
+    budget = int(1.2 * max(peak1, peak2))
+    results, stats = serve_all(alone, max_active=3, hbm_budget=budget)
+    assert stats["peak_bytes_held"] <= budget and stats["plans_evicted"] >= 1
+    for r, (F, info) in zip(alone, results):
+        assert np.array_equal(F, r["F"])
