@@ -127,12 +127,10 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + NB;
   // neighbour row offsets in flat index: -nx, +nx, -nx*ny, +nx*ny (present axes only)
-  int64_t off[4] = {0, 0, 0, 0};
-  {
-    int k = 0;
-    if (ny > 1) { off[k++] = -(int64_t)nx; off[k++] = nx; }
-    if (nz > 1) { off[k++] = -(int64_t)nx * ny; off[k++] = (int64_t)nx * ny; }
-  }
+  // (the order matches the neighbour flags: y pair first when the grid has a y axis)
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t off[4] = {ny > 1 ? -(int64_t)nx : -plane, ny > 1 ? (int64_t)nx : plane, -plane,
+                          plane};
   const int64_t G = gridDim.x;
   const int64_t lo = share_lo(a.T, blockIdx.x, G);
   const int64_t hi = share_lo(a.T, blockIdx.x + 1, G);

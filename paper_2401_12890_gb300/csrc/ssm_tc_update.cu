@@ -18,16 +18,26 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // tc_update_kernel: the z-step, dual step and next-w split, TMA-staged (HBM-bound).
-// Work items are (16-compartment chunk, voxel tile of 128) pairs ordered chunk-major, so
-// CTAs running at the same time hold the same compartments of neighbouring tiles and
-// the -+nx halo rows one CTA loads are the rows its neighbours load (L2 hits). A CTA
-// takes a contiguous share of the items; one producer warp streams z (x halo), its -+nx (-+nx*ny) neighbour
-// rows, d, h and acc for each chunk with 2D TMA boxes into a 2-stage mbarrier ring;
-// four consumer warps own a voxel per lane, compute the 16 compartments of the chunk,
-// store z' and d' (coalesced) and the 16 new w values of the voxel as one 32-byte BF16
-// hi/lo sector pair in the voxel-major w array.
-constexpr int UTV = 128, UQC = 16, UNB = 2, UNCW = 4;
-constexpr int UNT = 32 * (UNCW + 1);
+// Work items are (16-compartment chunk, voxel tile of 128) pairs ordered chunk-major and
+// dealt round-robin to the CTAs (item c to CTA c mod G), so the CTAs running at the same
+// time hold the same compartments of consecutive tiles: the -+nx and -+nx*ny halo rows
+// one CTA loads are the rows the CTAs of the neighbouring tiles load at about the same
+// time (L2 hits). One producer warp streams z (x halo), its neighbour rows, d, h and acc
+// for each item with 2D TMA boxes into a 2-stage mbarrier ring; the consumer warps (8
+// on 1D/2D grids, 16 on 3D grids) each own 32 voxels and one group of the chunk's
+// compartments (8, or 4), store z' and d' (coalesced) and the group's new w values of
+// each voxel as one 16- (8-) byte BF16 store each for hi and lo; the parts of a voxel's
+// 32-byte sector are written by warps of the same CTA moments apart, so L2 merges them
+// before writing the sector back.
+constexpr int UTV = 128, UQC = 16, UNB = 2;
+// consumer warps: 8 (2 compartment groups) on 1D/2D grids, 16 (4 groups) on 3D grids,
+// whose larger stage leaves room for one CTA per SM only
+template <int NCW>
+struct UWarps {
+  static constexpr int QG = NCW / 4;        // compartment groups of the chunk
+  static constexpr int QH = UQC / QG;       // compartments per consumer warp
+  static constexpr int NT = 32 * (NCW + 1); // + the producer warp
+};
 constexpr int UZW = UTV + 8, UNW = UTV + 4;
 
 struct UpdMaps {
@@ -66,9 +76,10 @@ __host__ __device__ __forceinline__ int64_t ufloor4(int64_t v) {
   return v >= 0 ? (v & ~(int64_t)3) : -(((-v) + 3) & ~(int64_t)3);
 }
 
-template <bool CHECK>
-__global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ UpdMaps maps,
-                                                        const UpdArgs a) {
+template <bool CHECK, int UNCW>
+__global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
+    const __grid_constant__ UpdMaps maps, const UpdArgs a) {
+  constexpr int UQH = UWarps<UNCW>::QH, UNT = UWarps<UNCW>::NT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
@@ -79,14 +90,11 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
   const ULayout L(NR);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + UNB;
-  int64_t off[4] = {0, 0, 0, 0};
-  {
-    int k = 0;
-    if (ny > 1) { off[k++] = -(int64_t)nx; off[k++] = nx; }
-    if (nz > 1) { off[k++] = -(int64_t)nx * ny; off[k++] = (int64_t)nx * ny; }
-  }
+  // (the order matches the neighbour flags: y pair first when the grid has a y axis)
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t off[4] = {ny > 1 ? -(int64_t)nx : -plane, ny > 1 ? (int64_t)nx : plane, -plane,
+                          plane};
   const int64_t G = gridDim.x;
-  const int64_t lo = (a.T * (int64_t)blockIdx.x) / G, hi = (a.T * ((int64_t)blockIdx.x + 1)) / G;
   const unsigned stage_bytes = (unsigned)(UQC * UZW * 4 + NR * UQC * UNW * 4 + 3 * UQC * UTV * 4);
   if (tid == 0) {
     for (int b = 0; b < UNB; ++b) {
@@ -101,8 +109,8 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
   if (warp == UNCW) {
     if (lane == 0) {
       tma_prefetch_map(&maps.zc);
-      for (int64_t c = lo; c < hi; ++c) {
-        const int i = (int)(c - lo), b = i % UNB, k = i / UNB;
+      for (int64_t c = blockIdx.x; c < a.T; c += G) {
+        const int i = (int)((c - blockIdx.x) / G), b = i % UNB, k = i / UNB;
         if (i >= UNB && !mbar_wait(&empty[b], (k - 1) & 1)) {
           failed = true;
           break;
@@ -122,12 +130,13 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
       }
     }
   } else {
-    const int v = warp * 32 + lane;
-    for (int64_t c = lo; c < hi; ++c) {
-      const int i = (int)(c - lo), b = i % UNB, k = i / UNB;
+    const int v = (warp & 3) * 32 + lane;   // voxel of this lane within the tile
+    const int qh = (warp >> 2) * UQH;         // first compartment of this warp's group
+    for (int64_t c = blockIdx.x; c < a.T; c += G) {
+      const int i = (int)((c - blockIdx.x) / G), b = i % UNB, k = i / UNB;
       if (!failed && !mbar_wait(&full[b], k & 1)) failed = true;
       const int64_t tile = c % a.ntiles;
-      const int q0 = (int)(c / a.ntiles) * UQC;
+      const int q0 = (int)(c / a.ntiles) * UQC + qh;
       const int64_t n0 = tile * UTV, n = n0 + v;
       const bool valid = n < N && !failed;
       int x = 0, y = 0, zc = 0;
@@ -151,11 +160,11 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
       const float* dr = reinterpret_cast<const float*>(st + L.dd);
       const float* hr = reinterpret_cast<const float*>(st + L.hh);
       const float* ar = reinterpret_cast<const float*>(st + L.aa);
-      float wv[UQC];
+      float wv[UQH];
 #pragma unroll
-      for (int r = 0; r < UQC; ++r) {
-        wv[r] = 0.f;
-        const int q = q0 + r;
+      for (int rr = 0; rr < UQH; ++rr) {
+        wv[rr] = 0.f;
+        const int r = qh + rr, q = q0 + rr;
         if (valid && q < a.Q) {
           const float z = zr[r * UZW + 4 + v], d = dr[r * UTV + v];
           float nb = 0.f;
@@ -170,7 +179,7 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
           const int64_t o = (int64_t)q * ld + n;
           a.Zout[o] = zn;
           a.Dout[o] = dn;
-          wv[r] = a.beta * zn - dn;
+          wv[rr] = a.beta * zn - dn;
           if (CHECK) {
             const float e = zn - f, ch = zn - z;
             s1 = fmaf(e, e, s1);
@@ -182,21 +191,22 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
       if (valid) {
-        // 16 values = one full 32-byte sector each for hi and lo
+        // UQH values = a part (a half or a quarter) of the voxel's 32-byte sector in hi
+        // and in lo
+        uint32_t hh[UQH / 2], ll[UQH / 2];
 #pragma unroll
-        for (int h2 = 0; h2 < UQC / 8; ++h2) {
-          uint32_t hh[4], ll[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float w0 = wv[8 * h2 + 2 * e], w1 = wv[8 * h2 + 2 * e + 1];
-            hh[e] = pack_bf16(w0, w1);
-            ll[e] = pack_bf16(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
-                              w1 - __bfloat162float(__float2bfloat16_rn(w1)));
-          }
-          *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0 + 8 * h2) =
-              make_uint4(hh[0], hh[1], hh[2], hh[3]);
-          *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0 + 8 * h2) =
-              make_uint4(ll[0], ll[1], ll[2], ll[3]);
+        for (int e = 0; e < UQH / 2; ++e) {
+          const float w0 = wv[2 * e], w1 = wv[2 * e + 1];
+          hh[e] = pack_bf16(w0, w1);
+          ll[e] = pack_bf16(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
+                            w1 - __bfloat162float(__float2bfloat16_rn(w1)));
+        }
+        if constexpr (UQH == 8) {
+          *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+          *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+        } else {
+          *reinterpret_cast<uint2*>(a.Whi + n * a.Qp + q0) = make_uint2(hh[0], hh[1]);
+          *reinterpret_cast<uint2*>(a.Wlo + n * a.Qp + q0) = make_uint2(ll[0], ll[1]);
         }
       }
     }
@@ -226,6 +236,23 @@ __global__ void __launch_bounds__(UNT) tc_update_kernel(const __grid_constant__ 
 
 int update_nr(const ssm_plan_s* pl) { return (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 ? 2 : 0); }
 
+// consumer warps of the kernel for this grid
+int update_ncw(const ssm_plan_s* pl) { return update_nr(pl) == 4 ? 16 : 8; }
+
+template <int NCW>
+int update_per_sm(int nr) {
+  const size_t shm = (size_t)ULayout(nr).total + 128;
+  const size_t shm_max = (size_t)ULayout(4).total + 128;
+  cudaFuncSetAttribute(tc_update_kernel<true, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)shm_max);
+  cudaFuncSetAttribute(tc_update_kernel<false, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)shm_max);
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_update_kernel<true, NCW>,
+                                                UWarps<NCW>::NT, shm);
+  return std::max(1, b);
+}
+
 int update_grid_impl(const ssm_plan_s* pl) {
   // resident CTAs per SM, per number of halo rows (the shared-memory layout differs)
   static std::atomic<int> cached[5];
@@ -235,15 +262,7 @@ int update_grid_impl(const ssm_plan_s* pl) {
     std::lock_guard<std::mutex> lock(attr_mutex());
     per_sm = cached[nr].load(std::memory_order_relaxed);
     if (per_sm == 0) {
-      const size_t shm = (size_t)ULayout(4).total + 128;
-      cudaFuncSetAttribute(tc_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)shm);
-      cudaFuncSetAttribute(tc_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)shm);
-      int b = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_update_kernel<true>, UNT,
-                                                    (size_t)ULayout(nr).total + 128);
-      per_sm = std::max(1, b);
+      per_sm = update_ncw(pl) == 16 ? update_per_sm<16>(nr) : update_per_sm<8>(nr);
       cached[nr].store(per_sm, std::memory_order_release);
     }
   }
@@ -291,10 +310,17 @@ ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* 
   const int grid = update_grid_impl(pl);
   *nparts = grid;
   const size_t shm = (size_t)ULayout(update_nr(pl)).total + 128;
-  if (check)
-    tc_update_kernel<true><<<grid, UNT, shm, s>>>(m, a);
-  else
-    tc_update_kernel<false><<<grid, UNT, shm, s>>>(m, a);
+  if (update_ncw(pl) == 16) {
+    if (check)
+      tc_update_kernel<true, 16><<<grid, UWarps<16>::NT, shm, s>>>(m, a);
+    else
+      tc_update_kernel<false, 16><<<grid, UWarps<16>::NT, shm, s>>>(m, a);
+  } else {
+    if (check)
+      tc_update_kernel<true, 8><<<grid, UWarps<8>::NT, shm, s>>>(m, a);
+    else
+      tc_update_kernel<false, 8><<<grid, UWarps<8>::NT, shm, s>>>(m, a);
+  }
   SSM_LAUNCHED();
   return SSM_OK;
 }

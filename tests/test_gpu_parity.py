@@ -112,6 +112,29 @@ def test_edge_cases_match_oracle(P, Q, dims, lam, beta, form, rank, pairs):
     assert err <= RTOL
 
 
+# Grid sizes (the launch-shape override) that cut the flattened (tile, compartment) rows
+# into shares straddling tile boundaries in different ways: few CTAs with many tiles
+# each, and more CTAs than tiles (tiles split into several segments whose partial u
+# are summed in the next iteration).
+@pytest.mark.parametrize("grid,P,Q,dims,tol,stop", [
+    (7, 14, 48, (20, 16, 12), 0.0, 40),     # 30 tiles over 7 CTAs, 205.7 rows each
+    (5, 10, 33, (40, 36), 0.0, 40),         # 12 tiles over 5 CTAs
+    (3, 12, 64, (30, 30, 9), 1e-3, 400),    # 64 tiles over 3 CTAs, with the stopping rule
+    (150, 14, 48, (20, 16, 12), 0.0, 40),   # more CTAs than tiles: 5 segments per tile
+])
+def test_lowrank_share_layouts_match_oracle(monkeypatch, grid, P, Q, dims, tol, stop):
+    monkeypatch.setenv("SSM_LOWRANK_GRID", str(grid))
+    K, M, _ = synth.random_problem(P, Q, dims, seed=grid * 7 + Q, snr=50.0)
+    F, info = gpu_solve(K, M, dims, 0.05, 1.0, form="lowrank", max_iter=stop,
+                        check_every=10 if tol else 0, tol_primal=tol, tol_change=tol)
+    ref = L.ladmm(K, M.astype(np.float32).astype(np.float64), dims, 0.05, 1.0,
+                  iters=stop, check_every=10 if tol else 0, tol_primal=tol, tol_change=tol)
+    assert info["iterations"] == ref["iters"]
+    err = rel(F, ref["z"])
+    print(f"grid {grid} dims {dims}: {info['iterations']} iterations, rel err {err:.3e}")
+    assert err <= RTOL
+
+
 def test_zero_iterations_returns_zero():
     K, M, _ = synth.random_problem(5, 6, (4, 4), seed=1)
     F, info = gpu_solve(K, M, (4, 4), 0.1, 1.0, max_iter=0)
