@@ -52,6 +52,12 @@ def parse_args():
     ap.add_argument("--ttt-repeats", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline form only")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-iters", type=int, default=100,
+                    help="iterations per served request (a fixed budget)")
+    ap.add_argument("--serve-load", type=float, default=0.7,
+                    help="Poisson arrival rate as a fraction of the measured capacity")
     return ap.parse_args()
 
 
@@ -342,6 +348,10 @@ def bench_ours(args):
     if dist.rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_and_errors(K, M, w, Md, F, make_plan, forms_to_run)
 
+    serving = None
+    if dist.world == 1 and not args.no_serving:
+        serving = bench_serving(args)
+
     if dist.rank == 0:
         hl = headline
         out = {
@@ -362,6 +372,7 @@ def bench_ours(args):
             "time_to_tol_ms": hl["rec"]["time_to_tol_ms"],
             "forms": results,
             "err_vs_oracle": cpu and cpu["errors"],
+            "serving": serving,
         }
         print(json.dumps(out), flush=True)
     dist.close()
@@ -393,6 +404,120 @@ def cpu_baseline_and_errors(K, M, w, Md, F, make_plan, forms):
             "rel_fro": float(np.linalg.norm(z - zr) / np.linalg.norm(zr))}
     return {"baseline": baseline, "errors": errors}
 
+
+
+# --------------------------------------------------------------------------------------
+# serving: Poisson-arriving solves of mixed shapes through the continuous-batching server
+# --------------------------------------------------------------------------------------
+SERVE_SHAPES = ["dr2d_tiny", "dr2d_slice", "rr3d_t1t2"]
+SERVE_FORMS = [("dense", "bf16x3"), ("lowrank", "fp32")]
+SERVE_SEED = 46
+
+
+def bench_serving(args):
+    """64 requests, shapes drawn uniformly from the tiny 2D, 2D slice and 3D T1-T2
+    workloads (seed 46), arriving as a Poisson process at `serve_load` of the measured
+    capacity; each request is a fixed budget of `serve_iters` iterations on host
+    buffers (M in, F out) through ssm_server_submit / ssm_server_wait. Returns the
+    latency percentiles and the aggregate throughput per form."""
+    import threading
+
+    import torch
+
+    from paper_2401_12890_gb300 import ssm, synth
+    rng = np.random.default_rng(SERVE_SEED)
+    kinds = rng.integers(0, len(SERVE_SHAPES), size=args.serve_requests)
+    data = {}
+    for name in SERVE_SHAPES:
+        w = synth.WORKLOADS[name]
+        K = synth.dictionary_for(name)
+        Ms = [torch.from_numpy(np.ascontiguousarray(
+            synth.make_problem(name, seed=w.seed + 100 * j)[1])).cuda() for j in range(2)]
+        data[name] = (w, K, Ms)
+    iters = args.serve_iters
+    out = {"requests": int(args.serve_requests), "iters_per_request": iters,
+           "mix": {n: int((kinds == i).sum()) for i, n in enumerate(SERVE_SHAPES)},
+           "shapes": {n: {"dims": list(data[n][0].dims), "P": data[n][0].P, "Q": data[n][0].Q}
+                      for n in SERVE_SHAPES},
+           "arrivals": f"Poisson (seed {SERVE_SEED}), rate = {args.serve_load:g} x capacity, "
+                       "capacity = 1 / mean solo service time of the mix",
+           "io": "device buffers: M resident on the device, F written to a fresh device "
+                 "buffer per request (ssm_server_submit_device)",
+           "forms": {}}
+    for form, prec in SERVE_FORMS:
+        key = form_key(form, prec)
+        kw = dict(form=form, precision=prec, max_iter=iters, check_every=0)
+        free, _ = torch.cuda.mem_get_info()
+        # plans get 60 % of the free memory; the rest holds the requests' F buffers
+        with ssm.Server(max_active=4, use_graphs=True, cache_plans=True,
+                        hbm_budget=int(0.6 * free)) as srv:
+            # solo service time per shape (plans built and cached here, as a server
+            # running before the measurement would have them)
+            solo = {}
+            for name in SERVE_SHAPES:
+                w, K, Ms = data[name]
+                times = []
+                for j in range(2):
+                    t = srv.submit(K, Ms[j], w.dims, w.lam, w.beta, **kw)
+                    times.append(srv.wait(t)[1]["latency_ms"])
+                solo[name] = times[-1]
+            mean_s = sum(solo[SERVE_SHAPES[k]] for k in kinds) / len(kinds) / 1e3
+            rate = args.serve_load / mean_s
+            gaps = rng.exponential(1.0 / rate, size=len(kinds))
+            arrivals = np.cumsum(gaps) - gaps[0]
+            s0 = srv.stats()
+            tickets = [None] * len(kinds)
+            t0 = time.perf_counter()
+
+            def submitter():
+                for i, k in enumerate(kinds):
+                    delay = t0 + arrivals[i] - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                    w, K, Ms = data[SERVE_SHAPES[k]]
+                    tickets[i] = srv.submit(K, Ms[i % 2], w.dims, w.lam, w.beta, **kw)
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            infos = []
+            for i in range(len(kinds)):
+                while tickets[i] is None:
+                    time.sleep(1e-4)
+                infos.append(srv.wait(tickets[i])[1])
+            th.join()
+            makespan = time.perf_counter() - t0
+            st = srv.stats()
+        lat = np.array([i["latency_ms"] for i in infos])
+        que = np.array([i["queue_ms"] for i in infos])
+        work = sum(data[SERVE_SHAPES[k]][0].N * data[SERVE_SHAPES[k]][0].Q * iters for k in kinds)
+        per_shape = {}
+        for i, name in enumerate(SERVE_SHAPES):
+            sel = lat[kinds == i]
+            if len(sel):
+                per_shape[name] = {"p50": float(np.percentile(sel, 50)),
+                                   "p99": float(np.percentile(sel, 99)),
+                                   "solo_ms": solo[name]}
+        out["forms"][key] = {
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99)), "mean": float(lat.mean())},
+            "queue_ms": {"p50": float(np.percentile(que, 50)),
+                         "p99": float(np.percentile(que, 99))},
+            "per_shape_latency_ms": per_shape,
+            "throughput": work / makespan, "unit": METRIC,
+            "requests_per_s": len(kinds) / makespan, "makespan_s": makespan,
+            "arrival_rate_per_s": rate,
+            "statuses_ok": int(sum(i["status"] in (ssm.SSM_OK, ssm.SSM_ENOTCONVERGED)
+                                   for i in infos)),
+            "plans_created": st["plans_created"] - s0["plans_created"],
+            "plans_reused": st["plans_reused"] - s0["plans_reused"],
+            "peak_hbm_reserved_gb": st["peak_bytes_held"] / 1e9,
+            "hbm_budget_gb": st["budget"] / 1e9,
+            "launch": "stream priority by footprint class (<= 64 MiB highest, one level per "
+                      "factor 4 above); above the first class, persistent kernels in 8 "
+                      "launch waves",
+        }
+        torch.cuda.empty_cache()
+    return out
 
 # --------------------------------------------------------------------------------------
 # reference arm: the FP64 oracle itself on the host cores

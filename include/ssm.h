@@ -120,6 +120,18 @@ ssm_status ssm_plan(ssm_plan_t* out, const ssm_params* p, const double* K_host,
                     int device, void* stream);
 
 /*
+ * ssm_plan with a launch setting (no counterpart in the paper): the solver's persistent
+ * kernels are launched with launch_waves (1..64) times as many CTAs as fit on the device
+ * at once, each doing 1/launch_waves of the work. 1 (what ssm_plan uses) gives the
+ * highest throughput; more waves make CTAs shorter-lived, so kernels on other streams,
+ * higher-priority ones first, get SMs within a fraction of a kernel's duration. Results
+ * are the same within rounding: the low-rank form sums its per-voxel partial products
+ * over a grid-dependent number of segments.
+ */
+ssm_status ssm_plan_ex(ssm_plan_t* out, const ssm_params* p, const double* K_host,
+                       int device, void* stream, int launch_waves);
+
+/*
  * Run the LADMM iteration (Algorithm 2, steps 4-12) on data M and write F = z.
  *   M_dev : P x N floats on the device, leading dimension ldm >= N; read only.
  *   F_dev : Q x N floats on the device, leading dimension ldf >= N; written.
@@ -233,12 +245,19 @@ ssm_status ssm_destroy(ssm_plan_t plan);
  * first-come first-served; a later request may pass a waiting one that does not fit
  * yet ("backfill"), but at most `max_bypass` times, after which admission waits for
  * memory to free up. Admitted solves run concurrently on their streams, so their
- * kernels overlap on the GPU. With `cache_plans`, a finished solve's plan (factors and
+ * kernels overlap on the GPU. Requests are ranked by footprint (the iteration is
+ * HBM-bound, so the footprint stands for the cost of an iteration): up to `small_bytes`
+ * is class 0, each factor of 4 above is one class more, up to the device's number of
+ * stream priorities, and a class-c request runs on a stream of the c-th highest
+ * priority. Requests above class 0 have their plans made by ssm_plan_ex(...,
+ * large_waves), so smaller solves get SMs within a fraction of a larger solve's
+ * kernel. With `cache_plans`, a finished solve's plan (factors and
  * state) stays resident; a later request with the same K, grid and plan parameters
  * (all of ssm_params except max_iter, check_every, tol_primal and tol_change) reuses
  * it without planning again. Idle plans are evicted least recently used first when a
  * new request needs their memory. Each request's result is exactly what ssm_solve_host
- * gives for it alone: the kernels and launch shapes do not depend on what else runs.
+ * (or ssm_solve) gives for it alone on a plan made with the same launch waves: the
+ * kernels and launch shapes do not depend on what else runs.
  * ------------------------------------------------------------------------------------
  */
 typedef struct ssm_server_s* ssm_server_t;
@@ -257,6 +276,8 @@ typedef struct {
                               its footprint for max_iter * simulate_us microseconds,
                               leaves F untouched and finishes with SSM_OK and 0
                               iterations. 0 = normal operation                      */
+  int64_t small_bytes;     /* footprint bound of the highest-priority class         */
+  int large_waves;         /* launch waves of the plans of larger requests, 1..64    */
 } ssm_server_config;
 
 typedef struct {
@@ -284,7 +305,7 @@ typedef struct {
 } ssm_server_stats;
 
 /* Defaults: device 0, 4 workers, 90 % of free memory, graphs on, plan cache on,
- * max_bypass 2 * max_active, normal operation. */
+ * max_bypass 2 * max_active, normal operation, small_bytes 64 MiB, large_waves 8. */
 ssm_status ssm_server_default_config(ssm_server_config* c);
 
 /* Create a server (threads and streams start here). */
@@ -301,6 +322,12 @@ ssm_status ssm_server_create(ssm_server_t* out, const ssm_server_config* c);
 ssm_status ssm_server_submit(ssm_server_t s, const ssm_params* p, const double* K_host,
                              const float* M_host, int64_t ldm, float* F_host, int64_t ldf,
                              int64_t* ticket);
+
+/* As ssm_server_submit with M and F in device memory on the server's device (the result
+ * stays on the device; no host copies). The reservation is the same. */
+ssm_status ssm_server_submit_device(ssm_server_t s, const ssm_params* p, const double* K_host,
+                                    const float* M_dev, int64_t ldm, float* F_dev,
+                                    int64_t ldf, int64_t* ticket);
 
 /* SSM_OK and *info filled (the solve's own status in info->status) once the request
  * has finished, after which the ticket is released; SSM_EPENDING while it has not;

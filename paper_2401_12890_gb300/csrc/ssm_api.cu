@@ -360,9 +360,11 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
 // (Gram matrix, eigenvectors, Jacobi scratch, K_r and the FP64 inverse). The low-rank
 // rank is known only after the eigendecomposition: without a fixed rank the bound
 // takes r = min(P, Q, 64), the largest the low-rank kernel supports.
-ssm_status footprint_impl(const ssm_params& p, bool staging, int64_t* persistent, int64_t* peak) {
+ssm_status footprint_impl(const ssm_params& p, bool staging, int waves, int64_t* persistent,
+                          int64_t* peak) {
   ssm_plan_s t;
   t.p = p;
+  t.waves = std::max(1, waves);
   t.P = p.P;
   t.Q = p.Q;
   t.g.nx = (int)p.dims[0];
@@ -665,11 +667,39 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
 
 }  // namespace
 
-ssm_status plan_footprint(const ssm_params& p, bool staging, int64_t* persistent, int64_t* peak) {
-  return footprint_impl(p, staging, persistent, peak);
+ssm_status plan_footprint(const ssm_params& p, bool staging, int waves, int64_t* persistent,
+                          int64_t* peak) {
+  return footprint_impl(p, staging, waves, persistent, peak);
 }
 
 ssm_status validate_params(const ssm_params* p) { return validate(p); }
+
+ssm_status plan_create(ssm_plan_t* out, const ssm_params* p, const double* K_host, int device,
+                       cudaStream_t s, int waves) {
+  if (!out) {
+    set_error("out is NULL");
+    return SSM_EINVAL;
+  }
+  *out = nullptr;
+  SSM_TRY(validate(p));
+  if (!K_host) {
+    set_error("K_host is NULL");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(device));
+  auto* pl = new ssm_plan_s();
+  pl->p = *p;
+  pl->device = device;
+  pl->waves = std::max(1, waves);
+  ssm_status st = plan_impl(pl, K_host, s);
+  if (st != SSM_OK) {
+    cudaStreamSynchronize(s);
+    release(pl);
+    return st;
+  }
+  *out = pl;
+  return SSM_OK;
+}
 
 }  // namespace ssm
 
@@ -697,29 +727,16 @@ ssm_status ssm_default_params(ssm_params* p) {
 
 ssm_status ssm_plan(ssm_plan_t* out, const ssm_params* p, const double* K_host, int device,
                     void* stream) {
-  if (!out) {
-    set_error("out is NULL");
+  return plan_create(out, p, K_host, device, static_cast<cudaStream_t>(stream), 1);
+}
+
+ssm_status ssm_plan_ex(ssm_plan_t* out, const ssm_params* p, const double* K_host, int device,
+                       void* stream, int launch_waves) {
+  if (launch_waves < 1 || launch_waves > 64) {
+    set_error("launch_waves must be in [1, 64]");
     return SSM_EINVAL;
   }
-  *out = nullptr;
-  SSM_TRY(validate(p));
-  if (!K_host) {
-    set_error("K_host is NULL");
-    return SSM_EINVAL;
-  }
-  SSM_CUDA(cudaSetDevice(device));
-  auto* pl = new ssm_plan_s();
-  pl->p = *p;
-  pl->device = device;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  ssm_status st = plan_impl(pl, K_host, s);
-  if (st != SSM_OK) {
-    cudaStreamSynchronize(s);
-    release(pl);
-    return st;
-  }
-  *out = pl;
-  return SSM_OK;
+  return plan_create(out, p, K_host, device, static_cast<cudaStream_t>(stream), launch_waves);
 }
 
 ssm_status ssm_solve(ssm_plan_t plan, const float* M_dev, int64_t ldm, float* F_dev, int64_t ldf,
@@ -832,7 +849,7 @@ ssm_status ssm_plan_footprint(const ssm_params* p, int device, int64_t* persiste
     return SSM_EINVAL;
   }
   SSM_CUDA(cudaSetDevice(device));
-  return footprint_impl(*p, true, persistent_bytes, peak_bytes);
+  return footprint_impl(*p, true, 1, persistent_bytes, peak_bytes);
 }
 
 ssm_status ssm_plan_device_bytes(ssm_plan_t plan, int64_t* bytes) {

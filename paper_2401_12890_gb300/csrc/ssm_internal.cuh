@@ -139,6 +139,9 @@ struct ssm_plan_s {
   size_t prof_used = 0;              // pairs recorded since the last read
   // device bytes the plan holds (every allocation it owns)
   int64_t bytes = 0;
+  // persistent grids are launched with `waves` times the resident CTAs (1 = one CTA per
+  // resident slot; more = shorter-lived CTAs, so other streams get SMs sooner)
+  int waves = 1;
   // iteration blocks replayed as CUDA graphs (ssm_plan_set_graphs)
   bool use_graphs = false;
   std::vector<ssm::GraphBlock> graphs;
@@ -148,7 +151,11 @@ namespace ssm {
 
 // parameter checks of ssm_plan; device bytes of a plan for p (see ssm_plan_footprint)
 ssm_status validate_params(const ssm_params* p);
-ssm_status plan_footprint(const ssm_params& p, bool staging, int64_t* persistent, int64_t* peak);
+ssm_status plan_footprint(const ssm_params& p, bool staging, int waves, int64_t* persistent,
+                          int64_t* peak);
+// ssm_plan with the launch-waves setting
+ssm_status plan_create(ssm_plan_t* out, const ssm_params* p, const double* K_host, int device,
+                       cudaStream_t s, int waves);
 
 // ------------------------------------------------------------------------------------
 // launchers (each returns a status; the stream is the caller's)

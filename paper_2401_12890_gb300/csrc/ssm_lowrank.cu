@@ -396,7 +396,7 @@ int64_t lowrank_grid(const ssm_plan_s* pl) {
   const int nr = (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 ? 2 : 0);
   const int64_t ntiles = (pl->g.N + TV - 1) / TV;
   const int64_t T = ntiles * pl->Q;
-  int64_t grid = (int64_t)sm_count() * bpsm_for(pl->R, nr);
+  int64_t grid = (int64_t)sm_count() * bpsm_for(pl->R, nr) * std::max(1, pl->waves);
   if (const char* env = getenv("SSM_LOWRANK_GRID")) {   // launch-shape override for sweeps
     const long v = atol(env);
     if (v >= 1 && v <= 65536) grid = v;

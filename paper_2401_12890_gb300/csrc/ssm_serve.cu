@@ -9,6 +9,16 @@
 // reused by a later request with the same dictionary, grid and plan parameters; idle
 // plans are evicted least recently used first when a request needs their memory.
 //
+// Latency classes: the iteration is HBM-bound, so a request's footprint stands for its
+// cost per iteration. A request whose footprint is at most `small_bytes` is class 0;
+// each factor of 4 above that is one class more, up to the number of stream priorities
+// the device offers. Every worker has one stream per priority and runs a class-c
+// request on the c-th highest. Requests above class 0 have their persistent kernels
+// launched as `large_waves` waves of CTAs: short-lived CTAs let the block scheduler
+// hand SMs to higher-priority streams every few hundred microseconds, so a small solve
+// arriving during a large one is not held up for the large one's kernels (which would
+// otherwise keep every SM for milliseconds).
+//
 // Memory accounting: every plan (running or idle) has a reservation, its peak
 // footprint while planning and its persistent footprint afterwards. `held` sums the
 // reservations of live plans, `dying` those of evicted plans not yet freed. A worker
@@ -69,6 +79,7 @@ uint64_t hash_doubles(const double* data, size_t n) {
 struct Resident {
   ssm_plan_t plan = nullptr;
   ssm_params p{};
+  int waves = 1;
   std::vector<double> K;     // the dictionary the plan was made from
   uint64_t khash = 0;
   int64_t bytes = 0;         // reservation
@@ -79,6 +90,9 @@ struct Resident {
 struct Request {
   int64_t ticket = 0;
   ssm_params p{};
+  bool device_io = false;    // M and F are device buffers
+  int level = 0;             // latency class: stream priority (0 = highest)
+  int waves = 1;
   const double* K = nullptr;
   const float* M = nullptr;
   int64_t ldm = 0;
@@ -114,7 +128,8 @@ struct ssm_server_s {
   bool stop = false;
   ssm_server_stats st{};
   std::vector<std::thread> workers;
-  std::vector<cudaStream_t> streams;
+  // streams[level][worker]: one stream per priority level and worker (level 0 = highest)
+  std::vector<std::vector<cudaStream_t>> streams;
 
   // choose a request to run (caller holds mu); fills the plan to use and the idle
   // plans to free first
@@ -124,7 +139,7 @@ struct ssm_server_s {
       Resident* match = nullptr;
       if (cfg.cache_plans)
         for (auto& r : residents)
-          if (!r->busy && r->khash == q->khash && same_plan(r->p, q->p) &&
+          if (!r->busy && r->khash == q->khash && r->waves == q->waves && same_plan(r->p, q->p) &&
               r->K.size() == (size_t)q->p.P * q->p.Q &&
               std::memcmp(r->K.data(), q->K, sizeof(double) * r->K.size()) == 0) {
             match = r.get();
@@ -165,6 +180,7 @@ struct ssm_server_s {
         } else {
           auto r = std::make_unique<Resident>();
           r->p = q->p;
+          r->waves = q->waves;
           r->khash = q->khash;
           r->bytes = need;
           r->busy = true;
@@ -186,17 +202,19 @@ struct ssm_server_s {
   // run one admitted request on `slot`'s stream; returns the solve's status
   ssm_status run(Request* q, Resident* res, int slot) {
     const bool sim = cfg.simulate_us > 0;
+    cudaStream_t stream = sim ? nullptr : streams[q->level][slot];
     if (!res->plan && !sim) {
       const Clock::time_point t0 = Clock::now();
       res->K.assign(q->K, q->K + (size_t)q->p.P * q->p.Q);
-      SSM_TRY(ssm_plan(&res->plan, &q->p, q->K, cfg.device, streams[slot]));
+      SSM_TRY(plan_create(&res->plan, &q->p, q->K, cfg.device, stream, q->waves));
       q->info.plan_ms = ms_between(t0, Clock::now());
       if (cfg.use_graphs) ssm_plan_set_graphs(res->plan, 1);
       // planning's temporaries are gone: keep only the persistent reservation
       ssm_params pr = q->p;
       if (pr.form == SSM_FORM_LOWRANK) pr.rank = res->plan->r;
       int64_t persistent = 0, peak_b = 0;
-      if (plan_footprint(pr, true, &persistent, &peak_b) == SSM_OK && persistent < res->bytes) {
+      if (plan_footprint(pr, true, q->waves, &persistent, &peak_b) == SSM_OK &&
+          persistent < res->bytes) {
         std::lock_guard<std::mutex> lk(mu);
         held -= res->bytes - persistent;
         res->bytes = persistent;
@@ -218,7 +236,8 @@ struct ssm_server_s {
     res->plan->p.tol_change = q->p.tol_change;
     ssm_info inf{};
     const ssm_status s =
-        ssm_solve_host(res->plan, q->M, q->ldm, q->F, q->ldf, &inf, streams[slot]);
+        q->device_io ? ssm_solve(res->plan, q->M, q->ldm, q->F, q->ldf, &inf, stream)
+                     : ssm_solve_host(res->plan, q->M, q->ldm, q->F, q->ldf, &inf, stream);
     q->info.iterations = inf.iterations;
     q->info.res_primal = inf.res_primal;
     q->info.res_change = inf.res_change;
@@ -311,6 +330,73 @@ ssm_status collect(ssm_server_s* s, std::unique_lock<std::mutex>& lk, int64_t ti
 
 }  // namespace
 
+namespace {
+
+ssm_status submit(ssm_server_t s, const ssm_params* p, const double* K_host, const float* M,
+                  int64_t ldm, float* F, int64_t ldf, bool device_io, int64_t* ticket) {
+  if (!s || !ticket || !K_host || !M || !F) {
+    set_error("NULL argument");
+    return SSM_EINVAL;
+  }
+  SSM_TRY(validate_params(p));
+  int64_t N = 1;
+  for (int d = 0; d < p->ndim; ++d) N *= p->dims[d];
+  if (ldm < N || ldf < N) {
+    set_error("leading dimension smaller than N");
+    return SSM_EINVAL;
+  }
+  auto q = std::make_unique<Request>();
+  q->p = *p;
+  q->device_io = device_io;
+  q->K = K_host;
+  q->M = M;
+  q->ldm = ldm;
+  q->F = F;
+  q->ldf = ldf;
+  q->khash = hash_doubles(K_host, (size_t)p->P * p->Q);
+  // the reservation always covers the host staging buffers, so that a resident plan can
+  // serve host and device requests alike
+  int64_t persistent = 0;
+  const bool sim = s->cfg.simulate_us > 0;
+  int prev = 0;
+  if (!sim) {
+    SSM_CUDA(cudaGetDevice(&prev));
+    SSM_CUDA(cudaSetDevice(s->cfg.device));
+  }
+  ssm_status fs = plan_footprint(*p, true, 1, &persistent, &q->footprint);
+  const int nlev = sim ? 1 : (int)s->streams.size();
+  for (int64_t b = std::max<int64_t>(1, s->cfg.small_bytes); q->footprint > b && q->level < nlev - 1;
+       b *= 4)
+    ++q->level;
+  if (fs == SSM_OK && q->footprint > s->cfg.small_bytes && s->cfg.large_waves > 1) {
+    q->waves = s->cfg.large_waves;
+    fs = plan_footprint(*p, true, q->waves, &persistent, &q->footprint);
+  }
+  if (sim)
+    cudaGetLastError();   // device queries made without a device leave a sticky error
+  else
+    cudaSetDevice(prev);
+  SSM_TRY(fs);
+  q->info.footprint = q->footprint;
+  std::lock_guard<std::mutex> lk(s->mu);
+  ++s->st.submitted;
+  if (q->footprint > s->budget) {
+    ++s->st.rejected;
+    set_error("request footprint (" + std::to_string(q->footprint) +
+              " bytes) exceeds the server's HBM budget (" + std::to_string(s->budget) + ")");
+    return SSM_ENOMEM;
+  }
+  q->ticket = s->next_ticket++;
+  q->t_submit = Clock::now();
+  *ticket = q->ticket;
+  s->pending.push_back(q.get());
+  s->requests[q->ticket] = std::move(q);
+  s->cv_work.notify_all();
+  return SSM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 ssm_status ssm_server_default_config(ssm_server_config* c) {
@@ -323,6 +409,8 @@ ssm_status ssm_server_default_config(ssm_server_config* c) {
   c->cache_plans = 1;
   c->max_bypass = -1;
   c->simulate_us = 0;
+  c->small_bytes = (int64_t)1 << 26;
+  c->large_waves = 8;
   return SSM_OK;
 }
 
@@ -334,6 +422,10 @@ ssm_status ssm_server_create(ssm_server_t* out, const ssm_server_config* c) {
   *out = nullptr;
   if (c->max_active < 1 || c->max_active > 256) {
     set_error("max_active must be in [1, 256]");
+    return SSM_EINVAL;
+  }
+  if (c->large_waves < 1 || c->large_waves > 64) {
+    set_error("large_waves must be in [1, 64]");
     return SSM_EINVAL;
   }
   auto s = std::make_unique<ssm_server_s>();
@@ -355,16 +447,21 @@ ssm_status ssm_server_create(ssm_server_t* out, const ssm_server_config* c) {
     if (e == cudaSuccess) {
       s->budget = c->hbm_budget > 0 ? std::min<int64_t>(c->hbm_budget, (int64_t)free_b)
                                     : (int64_t)(0.9 * (double)free_b);
-      s->streams.resize(c->max_active);
-      for (auto& st : s->streams) {
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-          set_error("cudaStreamCreateWithFlags failed");
-          for (auto& x : s->streams)
-            if (x) cudaStreamDestroy(x);
-          cudaSetDevice(prev);
-          return SSM_ECUDA;
-        }
-      }
+      int least = 0, greatest = 0;
+      cudaDeviceGetStreamPriorityRange(&least, &greatest);
+      const int nlev = std::max(1, least - greatest + 1);   // greatest is the numerically lowest
+      s->streams.assign(nlev, std::vector<cudaStream_t>(c->max_active, nullptr));
+      for (int l = 0; l < nlev; ++l)
+        for (int i = 0; i < c->max_active; ++i)
+          if (cudaStreamCreateWithPriority(&s->streams[l][i], cudaStreamNonBlocking,
+                                           greatest + l) != cudaSuccess) {
+            set_error("cudaStreamCreateWithPriority failed");
+            for (auto& v : s->streams)
+              for (auto& x : v)
+                if (x) cudaStreamDestroy(x);
+            cudaSetDevice(prev);
+            return SSM_ECUDA;
+          }
     }
     cudaSetDevice(prev);
     SSM_CUDA(e);
@@ -379,53 +476,13 @@ ssm_status ssm_server_create(ssm_server_t* out, const ssm_server_config* c) {
 ssm_status ssm_server_submit(ssm_server_t s, const ssm_params* p, const double* K_host,
                              const float* M_host, int64_t ldm, float* F_host, int64_t ldf,
                              int64_t* ticket) {
-  if (!s || !ticket || !K_host || !M_host || !F_host) {
-    set_error("NULL argument");
-    return SSM_EINVAL;
-  }
-  SSM_TRY(validate_params(p));
-  int64_t N = 1;
-  for (int d = 0; d < p->ndim; ++d) N *= p->dims[d];
-  if (ldm < N || ldf < N) {
-    set_error("leading dimension smaller than N");
-    return SSM_EINVAL;
-  }
-  auto q = std::make_unique<Request>();
-  q->p = *p;
-  q->K = K_host;
-  q->M = M_host;
-  q->ldm = ldm;
-  q->F = F_host;
-  q->ldf = ldf;
-  q->khash = hash_doubles(K_host, (size_t)p->P * p->Q);
-  int64_t persistent = 0;
-  if (s->cfg.simulate_us > 0) {
-    SSM_TRY(plan_footprint(*p, true, &persistent, &q->footprint));
-    cudaGetLastError();   // device queries made without a device leave a sticky error
-  } else {
-    int prev = 0;
-    SSM_CUDA(cudaGetDevice(&prev));
-    SSM_CUDA(cudaSetDevice(s->cfg.device));
-    const ssm_status fs = plan_footprint(*p, true, &persistent, &q->footprint);
-    cudaSetDevice(prev);
-    SSM_TRY(fs);
-  }
-  q->info.footprint = q->footprint;
-  std::lock_guard<std::mutex> lk(s->mu);
-  ++s->st.submitted;
-  if (q->footprint > s->budget) {
-    ++s->st.rejected;
-    set_error("request footprint (" + std::to_string(q->footprint) +
-              " bytes) exceeds the server's HBM budget (" + std::to_string(s->budget) + ")");
-    return SSM_ENOMEM;
-  }
-  q->ticket = s->next_ticket++;
-  q->t_submit = Clock::now();
-  *ticket = q->ticket;
-  s->pending.push_back(q.get());
-  s->requests[q->ticket] = std::move(q);
-  s->cv_work.notify_all();
-  return SSM_OK;
+  return submit(s, p, K_host, M_host, ldm, F_host, ldf, false, ticket);
+}
+
+ssm_status ssm_server_submit_device(ssm_server_t s, const ssm_params* p, const double* K_host,
+                                    const float* M_dev, int64_t ldm, float* F_dev, int64_t ldf,
+                                    int64_t* ticket) {
+  return submit(s, p, K_host, M_dev, ldm, F_dev, ldf, true, ticket);
 }
 
 ssm_status ssm_server_poll(ssm_server_t s, int64_t ticket, ssm_request_info* info) {
@@ -483,8 +540,9 @@ ssm_status ssm_server_destroy(ssm_server_t s) {
   if (!sim) cudaSetDevice(s->cfg.device);
   for (auto& r : s->residents)
     if (r->plan) ssm_destroy(r->plan);
-  for (auto& st : s->streams)
-    if (st) cudaStreamDestroy(st);
+  for (auto& v : s->streams)
+    for (auto& st : v)
+      if (st) cudaStreamDestroy(st);
   delete s;
   return SSM_OK;
 }

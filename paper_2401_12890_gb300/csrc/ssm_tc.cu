@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
 int gemm_grid(const ssm_plan_s* pl) {
   const int ntv = (int)((pl->g.N + BM - 1) / BM);
   const int ntq = (pl->Q + BN - 1) / BN;
-  return std::max(1, std::min(sm_count(), ntv * ntq));
+  return std::max(1, std::min(sm_count() * std::max(1, pl->waves), ntv * ntq));
 }
 
 }  // namespace

@@ -268,7 +268,8 @@ int update_grid_impl(const ssm_plan_s* pl) {
   }
   const int64_t ntiles = (pl->g.N + UTV - 1) / UTV;
   const int64_t T = ntiles * ((pl->Q + UQC - 1) / UQC);
-  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm, T));
+  return (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sm_count() * per_sm * std::max(1, pl->waves), T));
 }
 
 }  // namespace

@@ -56,6 +56,7 @@ class SsmServerConfig(ctypes.Structure):
         ("device", ctypes.c_int), ("max_active", ctypes.c_int), ("hbm_budget", ctypes.c_int64),
         ("use_graphs", ctypes.c_int), ("cache_plans", ctypes.c_int),
         ("max_bypass", ctypes.c_int), ("simulate_us", ctypes.c_int64),
+        ("small_bytes", ctypes.c_int64), ("large_waves", ctypes.c_int),
     ]
 
 
@@ -127,6 +128,10 @@ def load_library(path: str = LIB_PATH):
                                           ctypes.c_double, ctypes.c_int, dp, vp]
     lib.ssm_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.ssm_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
+    lib.ssm_plan_ex.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SsmParams), vp, ctypes.c_int, vp,
+                                ctypes.c_int]
+    lib.ssm_server_submit_device.argtypes = [vp, ctypes.POINTER(SsmParams), vp, vp, i64, vp, i64,
+                                             ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_plan_set_graphs.argtypes = [vp, ctypes.c_int]
     lib.ssm_plan_footprint.argtypes = [ctypes.POINTER(SsmParams), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -146,6 +151,7 @@ def load_library(path: str = LIB_PATH):
     for name in ("ssm_default_params", "ssm_plan", "ssm_solve", "ssm_solve_host",
                  "ssm_objective", "ssm_plan_factors", "ssm_destroy", "ssm_profile_enable",
                  "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
+                 "ssm_plan_ex", "ssm_server_submit_device",
                  "ssm_plan_footprint", "ssm_plan_device_bytes", "ssm_server_default_config",
                  "ssm_server_create", "ssm_server_submit", "ssm_server_poll", "ssm_server_wait",
                  "ssm_server_stats_read", "ssm_server_destroy"):
@@ -205,7 +211,7 @@ class Plan:
 
     def __init__(self, K, dims, lam, beta, *, form="lowrank", precision="fp32", rank=0,
                  rank_tol=5e-5, xi_p=0.0, stencil_pairs=2, max_iter=300, check_every=10,
-                 tol_primal=0.0, tol_change=0.0, device=0, stream=None):
+                 tol_primal=0.0, tol_change=0.0, device=0, stream=None, launch_waves=1):
         lib = load_library()
         K = np.ascontiguousarray(K, dtype=np.float64)
         p = make_params(K.shape[0], K.shape[1], dims, lam, beta, form=form,
@@ -219,8 +225,9 @@ class Plan:
         self.N = int(np.prod(dims))
         self.device = device
         self._h = ctypes.c_void_p()
-        st = lib.ssm_plan(ctypes.byref(self._h), ctypes.byref(p),
-                          K.ctypes.data_as(ctypes.c_void_p), int(device), _stream_handle(stream))
+        st = lib.ssm_plan_ex(ctypes.byref(self._h), ctypes.byref(p),
+                             K.ctypes.data_as(ctypes.c_void_p), int(device),
+                             _stream_handle(stream), int(launch_waves))
         if st != SSM_OK:
             raise SsmError(st, "ssm_plan")
 
@@ -335,13 +342,18 @@ class Server:
     """
 
     def __init__(self, *, device=0, max_active=4, hbm_budget=0, use_graphs=True,
-                 cache_plans=True, max_bypass=-1, simulate_us=0):
+                 cache_plans=True, max_bypass=-1, simulate_us=0, small_bytes=None,
+                 large_waves=None):
         lib = load_library()
         c = SsmServerConfig()
         lib.ssm_server_default_config(ctypes.byref(c))
         c.device, c.max_active, c.hbm_budget = int(device), int(max_active), int(hbm_budget)
         c.use_graphs, c.cache_plans = int(bool(use_graphs)), int(bool(cache_plans))
         c.max_bypass, c.simulate_us = int(max_bypass), int(simulate_us)
+        if small_bytes is not None:
+            c.small_bytes = int(small_bytes)
+        if large_waves is not None:
+            c.large_waves = int(large_waves)
         self._h = ctypes.c_void_p()
         st = lib.ssm_server_create(ctypes.byref(self._h), ctypes.byref(c))
         if st != SSM_OK:
@@ -349,20 +361,33 @@ class Server:
         self._keep = {}
 
     def submit(self, K, M, dims, lam, beta, *, out=None, **kw):
-        """K: P x Q (float64), M: P x N host array (float32). Returns a ticket."""
+        """K: P x Q (float64); M: P x N float32, a host array (F returned in a numpy
+        array) or a CUDA tensor (F returned in a CUDA tensor, nothing copied to the
+        host). Returns a ticket."""
         K = np.ascontiguousarray(K, dtype=np.float64)
-        M = np.ascontiguousarray(M, dtype=np.float32)
         P, Q = K.shape
         N = int(np.prod(dims))
-        assert M.shape == (P, N)
-        F = out if out is not None else np.empty((Q, N), dtype=np.float32)
-        assert F.dtype == np.float32 and F.flags.c_contiguous and F.shape == (Q, N)
         p = make_params(P, Q, dims, lam, beta, **kw)
         t = ctypes.c_int64()
-        st = load_library().ssm_server_submit(
-            self._h, ctypes.byref(p), K.ctypes.data_as(ctypes.c_void_p),
-            M.ctypes.data_as(ctypes.c_void_p), N, F.ctypes.data_as(ctypes.c_void_p), N,
-            ctypes.byref(t))
+        if hasattr(M, "is_cuda") and M.is_cuda:
+            import torch
+            assert M.dtype == torch.float32 and M.shape == (P, N) and M.stride(1) == 1
+            F = out if out is not None else torch.empty((Q, N), dtype=torch.float32,
+                                                        device=M.device)
+            assert F.is_cuda and F.stride(1) == 1 and F.shape == (Q, N)
+            st = load_library().ssm_server_submit_device(
+                self._h, ctypes.byref(p), K.ctypes.data_as(ctypes.c_void_p),
+                ctypes.c_void_p(M.data_ptr()), M.stride(0), ctypes.c_void_p(F.data_ptr()),
+                F.stride(0), ctypes.byref(t))
+        else:
+            M = np.ascontiguousarray(M, dtype=np.float32)
+            assert M.shape == (P, N)
+            F = out if out is not None else np.empty((Q, N), dtype=np.float32)
+            assert F.dtype == np.float32 and F.flags.c_contiguous and F.shape == (Q, N)
+            st = load_library().ssm_server_submit(
+                self._h, ctypes.byref(p), K.ctypes.data_as(ctypes.c_void_p),
+                M.ctypes.data_as(ctypes.c_void_p), N, F.ctypes.data_as(ctypes.c_void_p), N,
+                ctypes.byref(t))
         if st != SSM_OK:
             raise SsmError(st, "ssm_server_submit")
         self._keep[t.value] = (K, M, F)

@@ -32,9 +32,21 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def solve_alone(K, M, dims, lam, beta, graphs=False, **kw):
+SMALL_BYTES = 1 << 26      # the server's default bound of the highest-priority class
+LARGE_WAVES = 8            # and launch waves of larger requests
+
+
+def served_waves(K, dims, lam, beta, **kw):
+    """Launch waves the server gives this request (by its footprint)."""
+    kw = {k: v for k, v in kw.items() if k not in ("max_iter", "check_every", "tol_primal",
+                                                    "tol_change")}
+    _, peak = ssm.footprint(K.shape[0], K.shape[1], dims, lam=lam, beta=beta, **kw)
+    return 1 if peak <= SMALL_BYTES else LARGE_WAVES
+
+
+def solve_alone(K, M, dims, lam, beta, graphs=False, launch_waves=1, **kw):
     """One solve through ssm_solve_host on a private stream; (F, info, kernels launched)."""
-    plan = ssm.Plan(K, dims, lam, beta, **kw)
+    plan = ssm.Plan(K, dims, lam, beta, launch_waves=launch_waves, **kw)
     if graphs:
         plan.set_graphs(True)
     stream = torch.cuda.Stream()
@@ -137,8 +149,11 @@ def mixed_requests():
 def alone():
     reqs = mixed_requests()
     for r in reqs:
-        [(F, info, _)] = solve_alone(r["K"], r["M"], r["dims"], r["lam"], r["beta"], **r["kw"])
+        r["waves"] = served_waves(r["K"], r["dims"], r["lam"], r["beta"], **r["kw"])
+        [(F, info, _)] = solve_alone(r["K"], r["M"], r["dims"], r["lam"], r["beta"],
+                                     launch_waves=r["waves"], **r["kw"])
         r["F"], r["info"] = F, info
+    assert {r["waves"] for r in reqs} == {1, LARGE_WAVES}    # both classes in the mix
     return reqs
 
 
@@ -156,8 +171,23 @@ def serve_all(reqs, rounds=1, **server_kw):
     return out, stats
 
 
+@pytest.mark.parametrize("form", FORMS, ids=["lowrank", "dense_fp32", "dense_bf16x3"])
+@pytest.mark.parametrize("waves", [2, 8])
+def test_launch_waves_match_the_oracle(form, waves):
+    w = synth.WORKLOADS["dr2d_tiny"]
+    K, M, _ = synth.make_problem("dr2d_tiny")
+    [(F, info, _)] = solve_alone(K, M, w.dims, w.lam, w.beta, launch_waves=waves,
+                                 max_iter=200, check_every=0, **form)
+    ref = L.ladmm(K, M.astype(np.float64), w.dims, w.lam, w.beta,
+                  dense=form["form"] == "dense", iters=200, check_every=0)
+    err = rel(F, ref["z"])
+    print(f"{form} waves {waves}: rel err {err:.3e}")
+    assert err <= (1e-3 if form.get("precision") == "bf16x3" else RTOL)
+
+
 def test_served_results_equal_solo_results(alone):
-    results, stats = serve_all(alone, rounds=2, max_active=3)
+    results, stats = serve_all(alone, rounds=2, max_active=3, small_bytes=SMALL_BYTES,
+                               large_waves=LARGE_WAVES)
     n = len(alone)
     assert stats["completed"] == 2 * n and stats["failed"] == 0
     assert stats["plans_reused"] >= 1
@@ -170,8 +200,21 @@ def test_served_results_equal_solo_results(alone):
         assert info["latency_ms"] >= info["solve_ms"] > 0
 
 
+def test_device_buffers_give_the_same_results(alone):
+    out = []
+    with ssm.Server(max_active=3, small_bytes=SMALL_BYTES, large_waves=LARGE_WAVES) as srv:
+        tickets = [srv.submit(r["K"], torch.from_numpy(r["M"]).cuda(), r["dims"], r["lam"],
+                              r["beta"], **r["kw"]) for r in alone]
+        for t in tickets:
+            F, info = srv.wait(t)
+            assert F.is_cuda
+            out.append(F.cpu().numpy())
+    for r, F in zip(alone, out):
+        assert np.array_equal(F, r["F"])
+
+
 def test_served_results_match_the_oracle(alone):
-    results, _ = serve_all(alone, max_active=4)
+    results, _ = serve_all(alone, max_active=4, small_bytes=SMALL_BYTES, large_waves=LARGE_WAVES)
     for r, (F, info) in zip(alone, results):
         if not r.get("oracle"):
             continue
@@ -185,12 +228,18 @@ def test_served_results_match_the_oracle(alone):
 
 
 def test_tight_budget_serialises_and_evicts(alone):
-    _, peak1 = ssm.footprint(*alone[-1]["K"].shape, alone[-1]["dims"], lam=0.0, beta=1.0,
-                             form="dense", precision="bf16x3")
-    _, peak2 = ssm.footprint(*alone[-1]["K"].shape, alone[-1]["dims"], lam=0.0, beta=1.0,
-                             form="lowrank")
-    budget = int(1.2 * max(peak1, peak2))
-    results, stats = serve_all(alone, max_active=3, hbm_budget=budget)
+    # the server's reservation of the largest request: its footprint with its waves
+    biggest = 0
+    for r in alone:
+        srv_fp = None
+        with ssm.Server(max_active=1, hbm_budget=1 << 40, simulate_us=1, small_bytes=SMALL_BYTES,
+                        large_waves=LARGE_WAVES) as sim:
+            t = sim.submit(r["K"], r["M"], r["dims"], r["lam"], r["beta"], **r["kw"])
+            srv_fp = sim.wait(t)[1]["footprint"]
+        biggest = max(biggest, srv_fp)
+    budget = int(1.2 * biggest)
+    results, stats = serve_all(alone, max_active=3, hbm_budget=budget, small_bytes=SMALL_BYTES,
+                               large_waves=LARGE_WAVES)
     assert stats["peak_bytes_held"] <= budget and stats["plans_evicted"] >= 1
     for r, (F, info) in zip(alone, results):
         assert np.array_equal(F, r["F"])
