@@ -219,6 +219,35 @@ ssm_status ssm_profile_read(ssm_plan_t plan, double* main_kernel_ms,
 ssm_status ssm_plan_set_graphs(ssm_plan_t plan, int enable);
 
 /*
+ * Change the plan's beta without refactorising K (the spectral factors of Sec. III-D do
+ * not depend on beta): re-forms the weights of Eq. 28 (low-rank) or the inverse of
+ * Eq. 26 (dense) on `stream` and drops the plan's captured graphs. The next solve uses
+ * the new beta; xi_p (Eq. 32) does not depend on beta and is kept.
+ */
+ssm_status ssm_plan_set_beta(ssm_plan_t plan, double beta, void* stream);
+
+/*
+ * The beta heuristic of Sec. III-E: beta is tuned on the centre patch of the image
+ * (3 voxels per axis, starting at dims/2 - 1) and reused on the whole image. Each
+ * candidate beta_k = sigma_1^2 * 10^(grid_lo + (grid_hi - grid_lo) k / (n_grid - 1)),
+ * k = 0 .. n_grid-1, runs `iters` iterations of the low-rank form (rank and lambda as in
+ * `p`; the patch's own xi_p rule) from the zero start; the candidate with the lowest
+ * objective J(z) (Eq. 7 with K_r) wins, the smaller beta on a tie. The paper asks for
+ * the fastest convergence without fixing a measure: the lowest J after a fixed budget
+ * is the reading taken here.
+ *   p      : grid, P, Q, lambda, rank, rank_tol, stencil_pairs (beta, form, precision
+ *            and the stopping rule are ignored)
+ *   M_host : P x N floats (ldm >= N), host memory; only the patch's columns are read
+ *   betas, J : n_grid doubles each, may be NULL (the candidates and their objectives)
+ * One plan is made on the patch (one eigendecomposition); candidates differ only in
+ * their beta-dependent weights (ssm_plan_set_beta). Synchronises `stream`.
+ */
+ssm_status ssm_tune_beta(const ssm_params* p, const double* K_host, const float* M_host,
+                         int64_t ldm, int iters, int n_grid, double grid_lo, double grid_hi,
+                         int device, void* stream, double* beta_out, double* betas,
+                         double* J);
+
+/*
  * Device memory a plan for `p` would take on `device`, from the same sizes ssm_plan
  * allocates: *persistent_bytes = what the plan holds between calls, including the
  * staging buffers of ssm_solve_host; *peak_bytes = that plus the temporaries of

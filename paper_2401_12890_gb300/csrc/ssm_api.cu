@@ -841,6 +841,27 @@ ssm_status ssm_plan_set_graphs(ssm_plan_t plan, int enable) {
   return SSM_OK;
 }
 
+ssm_status ssm_plan_set_beta(ssm_plan_t plan, double beta, void* stream) {
+  if (!plan) {
+    set_error("NULL plan");
+    return SSM_EINVAL;
+  }
+  if (!(beta > 0.0) || !std::isfinite(beta)) {
+    set_error("beta must be > 0");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  plan->p.beta = beta;
+  // captured graphs hold the old beta in their kernel arguments
+  for (GraphBlock& b : plan->graphs)
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+  plan->graphs.clear();
+  SSM_TRY(beta_weights(plan, s));
+  if (plan->p.form == SSM_FORM_DENSE) SSM_TRY(form_dense_inverse(plan, s));
+  return SSM_OK;
+}
+
 ssm_status ssm_plan_footprint(const ssm_params* p, int device, int64_t* persistent_bytes,
                               int64_t* peak_bytes) {
   SSM_TRY(validate(p));

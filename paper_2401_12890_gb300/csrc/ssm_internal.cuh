@@ -166,6 +166,7 @@ ssm_status jacobi_eigen(double* A, int n, double* E, double* scratch, std::vecto
                         cudaStream_t s);
 ssm_status factors_fp64(ssm_plan_s* pl, const double* E, cudaStream_t s);
 ssm_status form_dense_inverse(ssm_plan_s* pl, cudaStream_t s);
+ssm_status beta_weights(ssm_plan_s* pl, cudaStream_t s);
 ssm_status project_data(const ssm_plan_s* pl, const float* M, int64_t ldm, int ncomp,
                         cudaStream_t s);
 ssm_status split_bf16(const float* X, int rows, int cols, int64_t ldx,

@@ -423,6 +423,24 @@ ssm_status factors_fp64(ssm_plan_s* pl, const double* E, cudaStream_t s) {
   SSM_CUDA(cudaMemcpyAsync(pl->alpha64, alpha.data(), sizeof(double) * n,
                            cudaMemcpyHostToDevice, s));
   SSM_CUDA(cudaStreamSynchronize(s));   // `alpha` is a host temporary
+  SSM_TRY(beta_weights(pl, s));
+  // dictionaries for the objective: K (FP32) and K_r = Bp_r Kt_r^T
+  to_f32<<<nblk((int64_t)P * Q, 256), 256, 0, s>>>(pl->K64, (int64_t)P * Q, pl->K32);
+  SSM_LAUNCHED();
+  double* Kr64 = nullptr;
+  SSM_CUDA(cudaMallocAsync(&Kr64, sizeof(double) * P * Q, s));
+  SSM_TRY(dgemm(P, Q, pl->r, pl->Bp64, n, false, pl->Kt64, n, true, Kr64, Q, s));
+  to_f32<<<nblk((int64_t)P * Q, 256), 256, 0, s>>>(Kr64, (int64_t)P * Q, pl->Kr32);
+  SSM_LAUNCHED();
+  SSM_CUDA(cudaFreeAsync(Kr64, s));
+  return SSM_OK;
+}
+
+// The beta-dependent part of the plan (the factors above do not depend on beta):
+// low-rank V_r and the weights of Eq. 28, or the dense form's h-map Gq; the dense
+// inverse itself is form_dense_inverse.
+ssm_status beta_weights(ssm_plan_s* pl, cudaStream_t s) {
+  const int Q = pl->Q, n = pl->n;
   const double floor = pl->sigma1 * 1e-15;
   if (pl->p.form == SSM_FORM_LOWRANK) {
     lowrank_basis<<<nblk((int64_t)Q * pl->R, 256), 256, 0, s>>>(
@@ -434,15 +452,6 @@ ssm_status factors_fp64(ssm_plan_s* pl, const double* E, cudaStream_t s) {
                                                         pl->Gq32);
     SSM_LAUNCHED();
   }
-  // dictionaries for the objective: K (FP32) and K_r = Bp_r Kt_r^T
-  to_f32<<<nblk((int64_t)P * Q, 256), 256, 0, s>>>(pl->K64, (int64_t)P * Q, pl->K32);
-  SSM_LAUNCHED();
-  double* Kr64 = nullptr;
-  SSM_CUDA(cudaMallocAsync(&Kr64, sizeof(double) * P * Q, s));
-  SSM_TRY(dgemm(P, Q, pl->r, pl->Bp64, n, false, pl->Kt64, n, true, Kr64, Q, s));
-  to_f32<<<nblk((int64_t)P * Q, 256), 256, 0, s>>>(Kr64, (int64_t)P * Q, pl->Kr32);
-  SSM_LAUNCHED();
-  SSM_CUDA(cudaFreeAsync(Kr64, s));
   return SSM_OK;
 }
 

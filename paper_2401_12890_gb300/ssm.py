@@ -133,6 +133,10 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_server_submit_device.argtypes = [vp, ctypes.POINTER(SsmParams), vp, vp, i64, vp, i64,
                                              ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_plan_set_graphs.argtypes = [vp, ctypes.c_int]
+    lib.ssm_plan_set_beta.argtypes = [vp, ctypes.c_double, vp]
+    lib.ssm_tune_beta.argtypes = [ctypes.POINTER(SsmParams), vp, vp, i64, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  vp, dp, vp, vp]
     lib.ssm_plan_footprint.argtypes = [ctypes.POINTER(SsmParams), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_plan_device_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
@@ -151,7 +155,8 @@ def load_library(path: str = LIB_PATH):
     for name in ("ssm_default_params", "ssm_plan", "ssm_solve", "ssm_solve_host",
                  "ssm_objective", "ssm_plan_factors", "ssm_destroy", "ssm_profile_enable",
                  "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
-                 "ssm_plan_ex", "ssm_server_submit_device",
+                 "ssm_plan_ex", "ssm_server_submit_device", "ssm_plan_set_beta",
+                 "ssm_tune_beta",
                  "ssm_plan_footprint", "ssm_plan_device_bytes", "ssm_server_default_config",
                  "ssm_server_create", "ssm_server_submit", "ssm_server_poll", "ssm_server_wait",
                  "ssm_server_stats_read", "ssm_server_destroy"):
@@ -206,6 +211,27 @@ def footprint(P, Q, dims, *, device=0, **kw):
     return a.value, b.value
 
 
+def tune_beta(K, M, dims, lam, *, iters=300, n_grid=15, grid_lo=-6.0, grid_hi=1.0, rank=0,
+              stencil_pairs=2, device=0, stream=None):
+    """The beta heuristic of Sec. III-E on the centre patch (ssm_tune_beta).
+    M: P x N host array. Returns (best beta, betas, objectives)."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float32)
+    P, Q = K.shape
+    p = make_params(P, Q, dims, lam, 1.0, rank=rank, stencil_pairs=stencil_pairs)
+    best = ctypes.c_double()
+    betas = np.zeros(n_grid)
+    J = np.zeros(n_grid)
+    st = load_library().ssm_tune_beta(
+        ctypes.byref(p), K.ctypes.data_as(ctypes.c_void_p), M.ctypes.data_as(ctypes.c_void_p),
+        M.shape[1], int(iters), int(n_grid), float(grid_lo), float(grid_hi), int(device),
+        _stream_handle(stream), ctypes.byref(best), betas.ctypes.data_as(ctypes.c_void_p),
+        J.ctypes.data_as(ctypes.c_void_p))
+    if st != SSM_OK:
+        raise SsmError(st, "ssm_tune_beta")
+    return best.value, betas, J
+
+
 class Plan:
     """A planned solver for one dictionary K (P x Q) and one voxel grid."""
 
@@ -230,6 +256,12 @@ class Plan:
                              _stream_handle(stream), int(launch_waves))
         if st != SSM_OK:
             raise SsmError(st, "ssm_plan")
+
+    def set_beta(self, beta, stream=None):
+        """Change beta without refactorising K (ssm_plan_set_beta)."""
+        st = load_library().ssm_plan_set_beta(self._h, float(beta), _stream_handle(stream))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_plan_set_beta")
 
     def set_graphs(self, enable=True):
         """Replay iteration blocks as CUDA graphs (ssm_plan_set_graphs)."""
