@@ -275,7 +275,8 @@ def bench_ours(args):
         per_step = ms_max / steps
         value = dist.world * N * Q * ITERS_PER_STEP / (per_step / 1e3)
         info = plan.solve(Md, F)[1]
-        rec = {"value": value, "ms_per_step": per_step,
+        launch = plan.launch_info()
+        rec = {"value": value, "ms_per_step": per_step, "launch": launch,
                "us_per_iteration": 1e3 * per_step / ITERS_PER_STEP,
                "rank": info["rank"], "gpu_launches": launches,
                "main_kernel_ms_avg": kms / max(kl, 1), "main_kernel_launches": kl}

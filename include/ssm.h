@@ -257,6 +257,19 @@ ssm_status ssm_tune_beta(const ssm_params* p, const double* K_host, const float*
 ssm_status ssm_plan_footprint(const ssm_params* p, int device, int64_t* persistent_bytes,
                               int64_t* peak_bytes);
 
+/* Launch configuration a plan uses (measurement support, no counterpart in the paper). */
+typedef struct {
+  int launch_waves;        /* see ssm_plan_ex                                        */
+  int gemm_tile_n;         /* tensor-core GEMM compartment-tile width (autotuned), 0
+                              when the plan has no tensor-core product              */
+  int gemm_grid;           /* CTAs of the tensor-core GEMM                           */
+  int update_grid;         /* CTAs of the tensor-core form's update kernel           */
+  int lowrank_grid;        /* CTAs of the fused low-rank kernel                      */
+  int sm_count;            /* SMs of the plan's device                               */
+} ssm_launch_info;
+
+ssm_status ssm_plan_launch_info(ssm_plan_t plan, ssm_launch_info* out);
+
 /* Device bytes the plan currently holds (every allocation it owns). */
 ssm_status ssm_plan_device_bytes(ssm_plan_t plan, int64_t* bytes);
 

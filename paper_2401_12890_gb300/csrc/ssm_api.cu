@@ -873,6 +873,25 @@ ssm_status ssm_plan_footprint(const ssm_params* p, int device, int64_t* persiste
   return footprint_impl(*p, true, 1, persistent_bytes, peak_bytes);
 }
 
+ssm_status ssm_plan_launch_info(ssm_plan_t plan, ssm_launch_info* out) {
+  if (!plan || !out) {
+    set_error("NULL argument");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(plan->device));
+  std::memset(out, 0, sizeof(*out));
+  out->launch_waves = plan->waves;
+  out->sm_count = sm_count();
+  if (plan->p.form == SSM_FORM_LOWRANK) {
+    out->lowrank_grid = (int)plan->lr_grid;
+  } else if (plan->Whi[0]) {
+    out->gemm_tile_n = plan->tc_bn;
+    out->gemm_grid = tc_gemm_grid(plan);
+    out->update_grid = tc_update_grid(plan);
+  }
+  return SSM_OK;
+}
+
 ssm_status ssm_plan_device_bytes(ssm_plan_t plan, int64_t* bytes) {
   if (!plan || !bytes) {
     set_error("NULL argument");

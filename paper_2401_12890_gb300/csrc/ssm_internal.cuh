@@ -142,6 +142,8 @@ struct ssm_plan_s {
   // persistent grids are launched with `waves` times the resident CTAs (1 = one CTA per
   // resident slot; more = shorter-lived CTAs, so other streams get SMs sooner)
   int waves = 1;
+  // compartment-tile width of the tensor-core GEMM (chosen by its autotuner)
+  int tc_bn = 256;
   // iteration blocks replayed as CUDA graphs (ssm_plan_set_graphs)
   bool use_graphs = false;
   std::vector<ssm::GraphBlock> graphs;
@@ -205,5 +207,6 @@ ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* 
                      cudaStream_t s);
 void tc_release(ssm_plan_s* pl);
 int tc_max_partials(const ssm_plan_s* pl);
+int tc_gemm_grid(const ssm_plan_s* pl);
 
 }  // namespace ssm

@@ -17,18 +17,22 @@
 //
 // GEMM operands: w is kept voxel-major (row n holds its Q compartments, stride Qp), so
 // both MMA operands are K-major: A = w tile (128 voxels x 64 compartments), B = M tile
-// (256 output compartments x 64), each a 128-byte-swizzled TMA box. The accumulator
-// (128 voxels x 256 compartments, FP32) lives in TMEM, with TMEM lanes = voxels, so
-// the epilogue's stores of acc into the map-major Q x N array coalesce.
+// (BN output compartments x 64), each a 128-byte-swizzled TMA box. The accumulator
+// (128 voxels x BN compartments, FP32) lives in TMEM, with TMEM lanes = voxels, so
+// the epilogue's stores of acc into the map-major Q x N array coalesce. The tile width
+// BN (128 .. 256) is chosen per problem shape by a small autotuner at plan time.
 //
 // GEMM schedule: one persistent CTA per SM walks (voxel tile, compartment tile) pairs,
 // voxel-tile major so concurrently running CTAs share w tiles in L2. Warp 0 issues TMA
 // loads into a smem ring; one thread of warp 1 issues the tcgen05.mma chain (3 MMAs
 // per K = 16 step) and commits stage releases and accumulator completions to
 // mbarriers; warps 2-5 drain the accumulator (tcgen05.ld) to global memory. Two
-// 256-column accumulators alternate so draining one tile overlaps the next tile's
-// MMAs. Every mbarrier wait is bounded.
+// accumulators (TMEM columns 0 and 256) alternate so draining one tile overlaps the
+// next tile's MMAs. Every mbarrier wait is bounded.
 #include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <tuple>
 
 #include "ssm_internal.cuh"
 #include "ssm_tma.cuh"
@@ -37,21 +41,32 @@ namespace ssm {
 namespace {
 
 constexpr int BM = 128;                         // voxels per tile (MMA M, TMEM lanes)
-constexpr int BN = 256;                         // compartments per tile (MMA N)
 constexpr int BK = 64;                          // K per stage: one 128-byte swizzle atom
 constexpr int UK = 16;                          // K per tcgen05.mma (kind::f16)
-constexpr int NS = 2;                           // smem stages
 constexpr int NTHR = 192;                       // TMA warp, MMA warp, 4 epilogue warps
-constexpr uint32_t TMEM_COLS = 512;             // two BN-column FP32 accumulators
+constexpr uint32_t TMEM_COLS = 512;             // two accumulators, at columns 0 and 256
 constexpr int A_BYTES = BM * BK * 2;            // 16 KB
-constexpr int B_BYTES = BN * BK * 2;            // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = NS * STAGE_BYTES + 1024 + 256;
+constexpr int kSmemLimit = 227 * 1024;
 
-// kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9,
-// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// Compartment-tile widths (MMA N) the autotuner chooses from: multiples of 32 (the
+// drain reads 32 TMEM columns at a time) up to 256 (one accumulator). Narrower tiles
+// waste fewer padded columns when Q is not a multiple of 256, and leave room for a
+// deeper smem ring.
+constexpr int kTileN[] = {256, 224, 192, 160, 128};
+
+template <int BN>
+struct Tile {
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int NS = (kSmemLimit - 2048) / STAGE_BYTES > 4 ? 4
+                                                                  : (kSmemLimit - 2048) / STAGE_BYTES;
+  static constexpr int SMEM_BYTES = NS * STAGE_BYTES + 1024 + 256;
+  // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9,
+  // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static_assert(BN % 32 == 0 && BN <= 256 && NS >= 2, "tile shape");
+};
 
 struct TcMaps {
   CUtensorMap a_hi, a_lo;   // w (voxel-major), box {BK, BM}
@@ -74,12 +89,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -114,8 +130,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <int BN>
 __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant__ TcMaps maps,
                                                           const TcArgs a) {
+  constexpr int NS = Tile<BN>::NS, STAGE_BYTES = Tile<BN>::STAGE_BYTES;
+  constexpr int B_BYTES = Tile<BN>::B_BYTES;
+  constexpr uint32_t IDESC = Tile<BN>::IDESC;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -187,7 +207,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
           break;
         }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
         for (int kc = 0; kc < nk; ++kc, ++c) {
           const int s = c % NS, r = c / NS;
           if (!mbar_wait(&full[s], r & 1)) {
@@ -202,9 +222,9 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
             const uint64_t alo = smem_desc(base + A_BYTES + kk * 32);
             const uint64_t bhi = smem_desc(base + 2 * A_BYTES + kk * 32);
             const uint64_t blo = smem_desc(base + 2 * A_BYTES + B_BYTES + kk * 32);
-            mma_bf16(d_tmem, ahi, bhi, (kc | kk) ? 1u : 0u);
-            mma_bf16(d_tmem, alo, bhi, 1u);
-            mma_bf16(d_tmem, ahi, blo, 1u);
+            mma_bf16(d_tmem, ahi, bhi, IDESC, (kc | kk) ? 1u : 0u);
+            mma_bf16(d_tmem, alo, bhi, IDESC, 1u);
+            mma_bf16(d_tmem, ahi, blo, IDESC, 1u);
           }
           mma_commit(&empty[s]);      // the stage is free once these MMAs complete
         }
@@ -228,7 +248,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
         const int q0 = qt * BN + cc * 32;
         if (q0 >= a.Q) break;                       // uniform across the warp
         float v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN + cc * 32),
+        tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 256 + cc * 32),
                   v);
         if (valid) {
 #pragma unroll
@@ -253,30 +273,14 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
   }
 }
 
-int gemm_grid(const ssm_plan_s* pl) {
+int gemm_grid(const ssm_plan_s* pl, int bn) {
   const int ntv = (int)((pl->g.N + BM - 1) / BM);
-  const int ntq = (pl->Q + BN - 1) / BN;
+  const int ntq = (pl->Q + bn - 1) / bn;
   return std::max(1, std::min(sm_count() * std::max(1, pl->waves), ntv * ntq));
 }
 
-}  // namespace
-
-ssm_status tc_prepare(ssm_plan_s* pl, cudaStream_t s) {
-  (void)s;
-  if (pl->Qp % BK != 0) {
-    set_error("tensor-core form: padded Q must be a multiple of 64");
-    return SSM_EUNSUPPORTED;
-  }
-  SSM_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                SMEM_BYTES));
-  return tc_update_prepare(pl);
-}
-
-int tc_max_partials(const ssm_plan_s* pl) { return std::max(gemm_grid(pl), tc_update_grid(pl)); }
-
-void tc_release(ssm_plan_s*) {}
-
-ssm_status tc_gemm(ssm_plan_s* pl, int cur, cudaStream_t s) {
+template <int BN>
+ssm_status launch_gemm(const ssm_plan_s* pl, int cur, cudaStream_t s) {
   const uint64_t Q = (uint64_t)pl->Q, N = (uint64_t)pl->g.N, Qp = (uint64_t)pl->Qp;
   TcMaps m;
   const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
@@ -292,10 +296,119 @@ ssm_status tc_gemm(ssm_plan_s* pl, int cur, cudaStream_t s) {
   a.Q = pl->Q;
   a.ntv = (int)((pl->g.N + BM - 1) / BM);
   a.ntq = (pl->Q + BN - 1) / BN;
-  tc_gemm_kernel<<<gemm_grid(pl), NTHR, SMEM_BYTES, s>>>(m, a);
+  tc_gemm_kernel<BN><<<gemm_grid(pl, BN), NTHR, Tile<BN>::SMEM_BYTES, s>>>(m, a);
   SSM_LAUNCHED();
   return SSM_OK;
 }
+
+ssm_status gemm_dispatch(const ssm_plan_s* pl, int bn, int cur, cudaStream_t s) {
+  switch (bn) {
+    case 256: return launch_gemm<256>(pl, cur, s);
+    case 224: return launch_gemm<224>(pl, cur, s);
+    case 192: return launch_gemm<192>(pl, cur, s);
+    case 160: return launch_gemm<160>(pl, cur, s);
+    case 128: return launch_gemm<128>(pl, cur, s);
+    default:
+      set_error("tensor-core GEMM: unsupported tile width");
+      return SSM_EUNSUPPORTED;
+  }
+}
+
+template <int BN>
+cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Tile<BN>::SMEM_BYTES);
+}
+
+// tile widths measured per (device, Q, N, waves), shared by every plan of the process
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int64_t, int>, int> g_tuned;
+
+// Autotuner: time every tile width on the plan's own operands (one warm-up launch, then
+// two timed launches each, CUDA events on the plan's stream) and keep the fastest.
+// The choice does not change results: each output element sums the same products in
+// the same K order whatever the tile width.
+ssm_status tune_tile(ssm_plan_s* pl, cudaStream_t s) {
+  if (const char* env = getenv("SSM_TC_BN")) {   // a fixed width (tests and sweeps)
+    const int v = atoi(env);
+    for (int bn : kTileN)
+      if (bn == v) {
+        pl->tc_bn = v;
+        return SSM_OK;
+      }
+  }
+  const auto key = std::make_tuple(pl->device, pl->Q, pl->g.N, pl->waves);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      pl->tc_bn = it->second;
+      return SSM_OK;
+    }
+  }
+  cudaEvent_t e0, e1;
+  SSM_CUDA(cudaEventCreate(&e0));
+  SSM_CUDA(cudaEventCreate(&e1));
+  int best = 256;
+  float best_ms = 0.f;
+  ssm_status st = SSM_OK;
+  for (int bn : kTileN) {
+    // a width whose tiles do not cover fewer padded columns than a wider one cannot win
+    const int pad = (pl->Q + bn - 1) / bn * bn;
+    if (bn != 256 && pad >= (pl->Q + 255) / 256 * 256) continue;
+    st = gemm_dispatch(pl, bn, 0, s);
+    if (st != SSM_OK) break;
+    if (cudaEventRecord(e0, s) != cudaSuccess) { st = SSM_ECUDA; break; }
+    for (int r = 0; r < 2 && st == SSM_OK; ++r) st = gemm_dispatch(pl, bn, 0, s);
+    if (st != SSM_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = SSM_ECUDA;
+      break;
+    }
+    if (bn == 256 || ms < best_ms) {
+      best = bn;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SSM_OK) return st;
+  pl->tc_bn = best;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned[key] = best;
+  return SSM_OK;
+}
+
+}  // namespace
+
+ssm_status tc_prepare(ssm_plan_s* pl, cudaStream_t s) {
+  if (pl->Qp % BK != 0) {
+    set_error("tensor-core form: padded Q must be a multiple of 64");
+    return SSM_EUNSUPPORTED;
+  }
+  SSM_CUDA(set_smem_attr<256>());
+  SSM_CUDA(set_smem_attr<224>());
+  SSM_CUDA(set_smem_attr<192>());
+  SSM_CUDA(set_smem_attr<160>());
+  SSM_CUDA(set_smem_attr<128>());
+  SSM_TRY(tc_update_prepare(pl));
+  return tune_tile(pl, s);
+}
+
+// reduction rows: bounded with the narrowest tile (the most tiles, the largest grid)
+int tc_max_partials(const ssm_plan_s* pl) {
+  return std::max(gemm_grid(pl, 128), tc_update_grid(pl));
+}
+
+void tc_release(ssm_plan_s*) {}
+
+ssm_status tc_gemm(ssm_plan_s* pl, int cur, cudaStream_t s) {
+  return gemm_dispatch(pl, pl->tc_bn, cur, s);
+}
+
+int tc_gemm_grid(const ssm_plan_s* pl) { return gemm_grid(pl, pl->tc_bn); }
 
 ssm_status tc_iteration(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
                         cudaStream_t s) {

@@ -87,6 +87,16 @@ class SsmServerStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class SsmLaunchInfo(ctypes.Structure):
+    _fields_ = [
+        ("launch_waves", ctypes.c_int), ("gemm_tile_n", ctypes.c_int), ("gemm_grid", ctypes.c_int),
+        ("update_grid", ctypes.c_int), ("lowrank_grid", ctypes.c_int), ("sm_count", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -133,6 +143,7 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_server_submit_device.argtypes = [vp, ctypes.POINTER(SsmParams), vp, vp, i64, vp, i64,
                                              ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_plan_set_graphs.argtypes = [vp, ctypes.c_int]
+    lib.ssm_plan_launch_info.argtypes = [vp, ctypes.POINTER(SsmLaunchInfo)]
     lib.ssm_plan_set_beta.argtypes = [vp, ctypes.c_double, vp]
     lib.ssm_tune_beta.argtypes = [ctypes.POINTER(SsmParams), vp, vp, i64, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -156,7 +167,7 @@ def load_library(path: str = LIB_PATH):
                  "ssm_objective", "ssm_plan_factors", "ssm_destroy", "ssm_profile_enable",
                  "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
                  "ssm_plan_ex", "ssm_server_submit_device", "ssm_plan_set_beta",
-                 "ssm_tune_beta",
+                 "ssm_tune_beta", "ssm_plan_launch_info",
                  "ssm_plan_footprint", "ssm_plan_device_bytes", "ssm_server_default_config",
                  "ssm_server_create", "ssm_server_submit", "ssm_server_poll", "ssm_server_wait",
                  "ssm_server_stats_read", "ssm_server_destroy"):
@@ -268,6 +279,14 @@ class Plan:
         st = load_library().ssm_plan_set_graphs(self._h, int(bool(enable)))
         if st != SSM_OK:
             raise SsmError(st, "ssm_plan_set_graphs")
+
+    def launch_info(self):
+        """Launch configuration (ssm_plan_launch_info): tile width, grids, waves."""
+        li = SsmLaunchInfo()
+        st = load_library().ssm_plan_launch_info(self._h, ctypes.byref(li))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_plan_launch_info")
+        return li.as_dict()
 
     def device_bytes(self):
         b = ctypes.c_int64()

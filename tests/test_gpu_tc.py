@@ -101,3 +101,25 @@ def test_full_size_slice_sampled_voxels_bf16x3():
         zref, flat = patch_reference(K, M.astype(np.float64), w.dims, w.lam, w.beta, xi, n_iter,
                                      c, "dense", None)
         assert rel(F[:, flat], zref) <= 1e-4, c
+
+
+# ---------------------------------------------------------------------------
+# GEMM tile widths (the autotuner's candidates): each forced width gives the same
+# product -- every output element sums the same K products in the same order -- so the
+# solve is bitwise the width-256 solve, which matches the oracle at the bf16x3 bar
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("P,Q,dims,iters", [(30, 225, (32, 32), 40), (12, 300, (9, 9, 5), 40),
+                                            (64, 1600, (40, 30), 20), (120, 2500, (24, 24), 12)])
+def test_gemm_tile_widths_agree(monkeypatch, P, Q, dims, iters):
+    K, M, _ = synth.random_problem(P, Q, dims, seed=Q, snr=50.0)
+    ref = None
+    for bn in (256, 224, 192, 160, 128):
+        monkeypatch.setenv("SSM_TC_BN", str(bn))
+        F, _, _ = run(K, M, dims, 0.02, 1.5, iters)
+        if ref is None:
+            ref = F
+            oracle = L.ladmm(K, M.astype(np.float32).astype(np.float64), dims, 0.02, 1.5,
+                             dense=True, iters=iters, check_every=0)
+            assert rel(F, oracle["z"]) <= 1e-3
+        else:
+            assert np.array_equal(F, ref), f"tile width {bn} differs from 256"
