@@ -351,11 +351,14 @@ int blocks_per_sm(int nr) {
   std::lock_guard<std::mutex> lock(attr_mutex());
   v = cached[nr].load(std::memory_order_relaxed);
   if (v != 0) return v;
+  // the attribute belongs to the kernel, not to the halo layout: allow the largest
+  // layout's size (3D, 4 halo rows), which every grid's launch fits in
   const size_t shm = smem_for<R>(nr);
+  const size_t shm_max = smem_for<R>(4);
   cudaFuncSetAttribute(lowrank_iter_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)shm);
+                       (int)shm_max);
   cudaFuncSetAttribute(lowrank_iter_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)shm);
+                       (int)shm_max);
   int b1 = 0, b2 = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, lowrank_iter_kernel<R, true>, NT, shm);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, lowrank_iter_kernel<R, false>, NT, shm);

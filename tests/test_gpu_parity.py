@@ -235,3 +235,19 @@ def test_full_size_slice_sampled_voxels(form):
         err = rel(F[:, flat], zref)
         assert err <= RTOL, (c, err)
     assert F.min() >= 0.0
+
+
+def test_lowrank_3d_after_2d_at_the_same_rank():
+    """The kernel's shared-memory limit is a property of the kernel, shared by every
+    grid: a 3D grid (4 halo rows) planned after a 2D grid (2 halo rows) at the same
+    padded rank must still launch."""
+    outs = []
+    for dims in ((6, 5, 4), (12, 10), (6, 5, 4)):
+        K, M, _ = synth.random_problem(40, 48, dims, seed=17, snr=50.0)
+        F, info = gpu_solve(K, M, dims, 0.05, 1.0, form="lowrank", rank=32, max_iter=20,
+                            check_every=0)
+        ref = L.ladmm(K, M.astype(np.float32).astype(np.float64), dims, 0.05, 1.0, rank=32,
+                      iters=20, check_every=0)
+        assert rel(F, ref["z"]) <= RTOL
+        outs.append(F)
+    assert np.array_equal(outs[0], outs[2])
