@@ -55,7 +55,13 @@ typedef enum {
 
 typedef enum {
   SSM_FORM_LOWRANK = 0,    /* Algorithm 2 with the rank-r f-step of Eq. 28          */
-  SSM_FORM_DENSE = 1       /* full-rank f-step of Eq. 26                            */
+  SSM_FORM_DENSE = 1,      /* full-rank f-step of Eq. 26                            */
+  SSM_FORM_ADMM = 2        /* Algorithm 1, the three-split ADMM the paper compares
+                              against (Sec. II-C): full-rank x-step, exact z-step by
+                              DCT-II diagonalisation of lambda D^T D + beta I (grid
+                              axes up to 256); FP32 only; F = y (the nonnegative
+                              split); residuals: ||f-x||^2+||f-y||^2+||f-z||^2 and
+                              ||y^{k+1}-y^k||^2, each relative to ||y||^2           */
 } ssm_form;
 
 typedef enum {

@@ -144,7 +144,7 @@ ssm_status validate(const ssm_params* p) {
     set_error("lambda must be >= 0");
     return SSM_EINVAL;
   }
-  if (p->form != SSM_FORM_LOWRANK && p->form != SSM_FORM_DENSE) {
+  if (p->form != SSM_FORM_LOWRANK && p->form != SSM_FORM_DENSE && p->form != SSM_FORM_ADMM) {
     set_error("unknown form");
     return SSM_EINVAL;
   }
@@ -187,6 +187,11 @@ void release(ssm_plan_s* pl) {
     dfree(pl->Whi[i]);
     dfree(pl->Wlo[i]);
   }
+  for (float** v : {&pl->adm.x, &pl->adm.y, &pl->adm.z, &pl->adm.dx, &pl->adm.dy, &pl->adm.dz,
+                    &pl->adm.f, &pl->adm.w, &pl->adm.r, &pl->adm.t, &pl->adm_D})
+    dfree(*v);
+  for (auto& tt : pl->adm_T)
+    for (float*& v : tt) dfree(v);
   dfree(pl->C32);
   dfree(pl->S);
   dfree(pl->H);
@@ -282,6 +287,13 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
     pl->r = n;
     pl->R = 0;
   }
+  if (p.form == SSM_FORM_ADMM && p.precision != SSM_FP32) {
+    cudaFreeAsync(A, s);
+    cudaFreeAsync(E, s);
+    cudaFreeAsync(scratch, s);
+    set_error("the ADMM form runs in FP32 only");
+    return SSM_EUNSUPPORTED;
+  }
   pl->Qp = (int)round_up(Q, 64);
 
   SSM_TRY(palloc(pl, &pl->Bp64, (size_t)P * n, s));
@@ -307,16 +319,34 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   cudaFreeAsync(E, s);
   cudaFreeAsync(scratch, s);
   if (st != SSM_OK) return st;
-  if (p.form == SSM_FORM_DENSE) SSM_TRY(form_dense_inverse(pl, s));
+  if (p.form != SSM_FORM_LOWRANK) SSM_TRY(form_dense_inverse(pl, s));
 
   // per-voxel state
   const size_t QN = (size_t)Q * pl->g.ld;
-  for (int i = 0; i < 2; ++i) {
-    SSM_TRY(palloc(pl, &pl->Z[i], QN, s));
-    SSM_TRY(palloc(pl, &pl->Dl[i], QN, s));
-  }
+  if (p.form != SSM_FORM_ADMM)
+    for (int i = 0; i < 2; ++i) {
+      SSM_TRY(palloc(pl, &pl->Z[i], QN, s));
+      SSM_TRY(palloc(pl, &pl->Dl[i], QN, s));
+    }
   int maxparts = 1;
-  if (p.form == SSM_FORM_LOWRANK) {
+  if (p.form == SSM_FORM_ADMM) {
+    AdmmState& a = pl->adm;
+    for (float** v : {&a.x, &a.y, &a.z, &a.dx, &a.dy, &a.dz, &a.f, &a.w, &a.r, &a.t})
+      SSM_TRY(palloc(pl, v, QN, s));
+    SSM_TRY(palloc(pl, &pl->C32, (size_t)n * pl->g.ld, s));
+    SSM_TRY(palloc(pl, &pl->H, QN, s));
+    SSM_TRY(palloc(pl, &pl->Acc, QN, s));
+    std::vector<std::pair<float**, std::vector<float>>> tables;
+    SSM_TRY(admm_tables(pl, &tables));
+    for (auto& t : tables) {
+      SSM_TRY(palloc(pl, t.first, t.second.size(), s));
+      SSM_CUDA(cudaMemcpyAsync(*t.first, t.second.data(), sizeof(float) * t.second.size(),
+                               cudaMemcpyHostToDevice, s));
+    }
+    SSM_CUDA(cudaStreamSynchronize(s));   // the host tables are temporaries
+    SSM_TRY(admm_prepare());
+    maxparts = std::max(admm_partial_rows(pl), dense_max_partials(pl));
+  } else if (p.form == SSM_FORM_LOWRANK) {
     SSM_TRY(palloc(pl, &pl->S, (size_t)pl->R * pl->g.ld, s));
     pl->lr_grid = lowrank_grid(pl);
     const size_t pf = (size_t)lowrank_partial_floats(pl, pl->lr_grid);
@@ -344,10 +374,10 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   maxparts = std::max(maxparts, (int)((pl->g.N + 255) / 256));  // objective partials
   pl->red_cap = maxparts;
   SSM_TRY(palloc(pl, &pl->red, (size_t)maxparts * 4, s));
-  SSM_TRY(palloc(pl, &pl->red_out, 4, s));
+  SSM_TRY(palloc(pl, &pl->red_out, 8, s));
   SSM_TRY(palloc(pl, &pl->dev_err, 1, s));
   SSM_CUDA(cudaMemsetAsync(pl->dev_err, 0, sizeof(int), s));
-  SSM_CUDA(cudaMallocHost(&pl->red_host, 4 * sizeof(double)));
+  SSM_CUDA(cudaMallocHost(&pl->red_host, 8 * sizeof(double)));
   SSM_CUDA(cudaEventRecord(pl->ev1, s));
   SSM_CUDA(cudaEventSynchronize(pl->ev1));
   SSM_CUDA(cudaEventElapsedTime(&pl->plan_ms, pl->ev0, pl->ev1));
@@ -401,9 +431,18 @@ ssm_status footprint_impl(const ssm_params& p, bool staging, int waves, int64_t*
     if (p.precision == SSM_BF16X3) add(2, 2 * Q * t.Qp);  // Mhi, Mlo
   }
   const int64_t QN = Q * ld;
-  add(4, 4 * QN);                             // Z[2], Dl[2]
+  if (p.form != SSM_FORM_ADMM) add(4, 4 * QN);  // Z[2], Dl[2]
   int64_t maxparts = 1;
-  if (p.form == SSM_FORM_LOWRANK) {
+  if (p.form == SSM_FORM_ADMM) {
+    add(4, 10 * QN);                          // x, y, z, d_x, d_y, d_z, f, w, r, t
+    add(4, n * ld);                           // C32
+    add(4, 2 * QN);                           // H, Acc
+    const int64_t dd[3] = {t.g.nx, t.g.ny, t.g.nz};
+    for (int d = 0; d < 3; ++d)
+      if (dd[d] > 1) add(4, 2 * dd[d] * 64 * ((dd[d] + 63) / 64));  // DCT tables
+    add(4, t.g.N);                            // spectral scaling
+    maxparts = std::max<int64_t>(admm_partial_rows(&t), dense_max_partials(&t));
+  } else if (p.form == SSM_FORM_LOWRANK) {
     add(4, (int64_t)t.R * ld);                // S
     t.lr_grid = lowrank_grid(&t);
     add(4, 2 * lowrank_partial_floats(&t, t.lr_grid));  // U[2]
@@ -422,12 +461,12 @@ ssm_status footprint_impl(const ssm_params& p, bool staging, int waves, int64_t*
   }
   maxparts = std::max<int64_t>(maxparts, (t.g.N + 255) / 256);
   add(8, maxparts * 4);                       // red
-  add(8, 4);                                  // red_out
+  add(8, 8);                                  // red_out
   add(4, 1);                                  // dev_err
   if (staging) add(4, (P + Q) * ld);          // Mstage, Fstage
   *persistent = b;
   int64_t tmp = 8 * (3 * n * n + 2) + 4 * n + 8 * P * Q;  // A, E, scratch, perm, K_r
-  if (p.form == SSM_FORM_DENSE) tmp += 8 * (n + Q * Q);   // inverse weights, FP64 inverse
+  if (p.form != SSM_FORM_LOWRANK) tmp += 8 * (n + Q * Q);   // inverse weights, FP64 inverse
   *peak = b + tmp;
   return SSM_OK;
 }
@@ -443,10 +482,19 @@ ssm_status check_device_error(ssm_plan_s* pl, int host_err) {
 }
 
 ssm_status read_residuals(ssm_plan_s* pl, int nparts, cudaStream_t s, double* rp, double* rc) {
-  SSM_TRY(finish_partials(pl->red, nparts, 3, pl->red_out, s));
-  SSM_CUDA(cudaMemcpyAsync(pl->red_host, pl->red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost,
-                           s));
-  int* herr = reinterpret_cast<int*>(pl->red_host + 3);
+  const bool admm = pl->p.form == SSM_FORM_ADMM;
+  int nsum = 3;
+  if (admm) {
+    // rows [0, nparts): ||f-y||^2, ||dy||^2, ||y||^2; rows [nparts, 2 nparts): ||f-x||^2, ||f-z||^2
+    SSM_TRY(finish_partials(pl->red, nparts, 3, pl->red_out, s));
+    SSM_TRY(finish_partials(pl->red + (int64_t)nparts * 4, nparts, 2, pl->red_out + 3, s));
+    nsum = 5;
+  } else {
+    SSM_TRY(finish_partials(pl->red, nparts, 3, pl->red_out, s));
+  }
+  SSM_CUDA(cudaMemcpyAsync(pl->red_host, pl->red_out, nsum * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+  int* herr = reinterpret_cast<int*>(pl->red_host + 7);
   SSM_CUDA(cudaMemcpyAsync(herr, pl->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   SSM_CUDA(cudaStreamSynchronize(s));
   if (*herr != 0) {
@@ -455,13 +503,20 @@ ssm_status read_residuals(ssm_plan_s* pl, int nparts, cudaStream_t s, double* rp
     SSM_CUDA(cudaMemsetAsync(pl->dev_err, 0, sizeof(int), s));
     return check_device_error(pl, e);
   }
-  const double zn = std::max(pl->red_host[2], 1e-300);
-  *rp = std::sqrt(pl->red_host[0] / zn);
-  *rc = std::sqrt(pl->red_host[1] / zn);
-  if (!std::isfinite(pl->red_host[0]) || !std::isfinite(pl->red_host[1]) ||
-      !std::isfinite(pl->red_host[2])) {
-    set_error("residual is not finite");
-    return SSM_ENAN;
+  const double* h = pl->red_host;
+  for (int i = 0; i < nsum; ++i)
+    if (!std::isfinite(h[i])) {
+      set_error("residual is not finite");
+      return SSM_ENAN;
+    }
+  if (admm) {
+    const double yn = std::max(h[2], 1e-300);
+    *rp = std::sqrt((h[0] + h[3] + h[4]) / yn);
+    *rc = std::sqrt(h[1] / yn);
+  } else {
+    const double zn = std::max(h[2], 1e-300);
+    *rp = std::sqrt(h[0] / zn);
+    *rc = std::sqrt(h[1] / zn);
   }
   return SSM_OK;
 }
@@ -483,6 +538,13 @@ ssm_status prof_mark(ssm_plan_s* pl, bool start, cudaStream_t s) {
 ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, bool check_next, int* nparts,
                          cudaStream_t s) {
   const ssm_params& p = pl->p;
+  if (p.form == SSM_FORM_ADMM) {
+    // the event pair brackets the whole iteration (elementwise steps, the x-step
+    // product, the z-step transforms)
+    SSM_TRY(prof_mark(pl, true, s));
+    SSM_TRY(admm_iteration(pl, check, pl->red, nparts, s));
+    return prof_mark(pl, false, s);
+  }
   SSM_TRY(prof_mark(pl, true, s));
   if (p.form == SSM_FORM_LOWRANK) {
     SSM_TRY(lowrank_iteration(pl, cur, check, check_next, pl->red, nparts, s));
@@ -601,9 +663,15 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
       SSM_CUDA(cudaMemsetAsync(pl->Wlo[0], 0, sizeof(__nv_bfloat16) * WN, s));
     }
   }
-  // step 2: z = d = 0
-  SSM_CUDA(cudaMemsetAsync(pl->Z[0], 0, sizeof(float) * QN, s));
-  SSM_CUDA(cudaMemsetAsync(pl->Dl[0], 0, sizeof(float) * QN, s));
+  // step 2: z = d = 0 (Algorithm 1: x = y = z = d_x = d_y = d_z = 0)
+  if (p.form == SSM_FORM_ADMM) {
+    const AdmmState& a = pl->adm;
+    for (float* v : {a.x, a.y, a.z, a.dx, a.dy, a.dz})
+      SSM_CUDA(cudaMemsetAsync(v, 0, sizeof(float) * QN, s));
+  } else {
+    SSM_CUDA(cudaMemsetAsync(pl->Z[0], 0, sizeof(float) * QN, s));
+    SSM_CUDA(cudaMemsetAsync(pl->Dl[0], 0, sizeof(float) * QN, s));
+  }
 
   const bool use_tol = p.tol_primal > 0 || p.tol_change > 0;
   int cur = 0, k = 0;
@@ -646,8 +714,9 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
     }
   }
   if (use_tol && !converged) result = SSM_ENOTCONVERGED;
-  // F = z (the feasible iterate)
-  SSM_CUDA(cudaMemcpy2DAsync(F, sizeof(float) * ldf, pl->Z[cur], sizeof(float) * ld,
+  // F = z (the feasible iterate; y for Algorithm 1)
+  const float* Fsrc = p.form == SSM_FORM_ADMM ? pl->adm.y : pl->Z[cur];
+  SSM_CUDA(cudaMemcpy2DAsync(F, sizeof(float) * ldf, Fsrc, sizeof(float) * ld,
                              sizeof(float) * pl->g.N, pl->Q, cudaMemcpyDeviceToDevice, s));
   if (info) {
     SSM_CUDA(cudaStreamSynchronize(s));
@@ -794,7 +863,7 @@ ssm_status ssm_objective(ssm_plan_t plan, const float* M_dev, int64_t ldm, const
   if (!plan->Res) SSM_TRY(palloc(plan, &plan->Res, (size_t)plan->P * ld, s));
   SSM_CUDA(cudaMemcpy2DAsync(plan->Res, sizeof(float) * ld, M_dev, sizeof(float) * ldm,
                              sizeof(float) * plan->g.N, plan->P, cudaMemcpyDeviceToDevice, s));
-  const float* Kd = (use_full_k || plan->p.form == SSM_FORM_DENSE) ? plan->K32 : plan->Kr32;
+  const float* Kd = (use_full_k || plan->p.form != SSM_FORM_LOWRANK) ? plan->K32 : plan->Kr32;
   // Res = M - K' F
   SSM_TRY(sgemm(plan->P, (int)plan->g.N, plan->Q, -1.f, Kd, plan->Q, F_dev, ldf, 1.f, plan->Res,
                 ld, s));
@@ -858,7 +927,17 @@ ssm_status ssm_plan_set_beta(ssm_plan_t plan, double beta, void* stream) {
     if (b.exec) cudaGraphExecDestroy(b.exec);
   plan->graphs.clear();
   SSM_TRY(beta_weights(plan, s));
-  if (plan->p.form == SSM_FORM_DENSE) SSM_TRY(form_dense_inverse(plan, s));
+  if (plan->p.form != SSM_FORM_LOWRANK) SSM_TRY(form_dense_inverse(plan, s));
+  if (plan->p.form == SSM_FORM_ADMM) {
+    // the z-step's spectral scaling 1 / (lambda s mu + beta) depends on beta
+    std::vector<std::pair<float**, std::vector<float>>> tables;
+    SSM_TRY(admm_tables(plan, &tables));
+    for (auto& t : tables)
+      if (t.first == &plan->adm_D)
+        SSM_CUDA(cudaMemcpyAsync(plan->adm_D, t.second.data(), sizeof(float) * t.second.size(),
+                                 cudaMemcpyHostToDevice, s));
+    SSM_CUDA(cudaStreamSynchronize(s));   // the host tables are temporaries
+  }
   return SSM_OK;
 }
 

@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -65,6 +66,12 @@ struct Grid {
 
 // the largest padded rank the fused low-rank kernel is instantiated for
 constexpr int kMaxRank = 64;
+
+// the device state of Algorithm 1 (map-major Q x ld arrays)
+struct AdmmState {
+  float *x, *y, *z, *dx, *dy, *dz;   // splits and duals
+  float *f, *w, *r, *t;              // f, w = beta f - d_x, r = beta f - d_z, transform scratch
+};
 
 // a block of iterations captured once and replayed as a CUDA graph; `key` holds the
 // start parity, the block length and each iteration's (test, next test) flags
@@ -144,6 +151,10 @@ struct ssm_plan_s {
   int waves = 1;
   // compartment-tile width of the tensor-core GEMM (chosen by its autotuner)
   int tc_bn = 256;
+  // Algorithm 1 (SSM_FORM_ADMM): state, per-axis DCT matrices (forward, inverse), scaling
+  ssm::AdmmState adm{};
+  float* adm_T[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  float* adm_D = nullptr;
   // iteration blocks replayed as CUDA graphs (ssm_plan_set_graphs)
   bool use_graphs = false;
   std::vector<ssm::GraphBlock> graphs;
@@ -195,6 +206,13 @@ ssm_status finish_partials(const double* partial, int nparts, int width, double*
                            cudaStream_t s);
 ssm_status objective_terms(const ssm_plan_s* pl, const float* Res, int P, const float* F,
                            int64_t ldf, double* partial, int* nparts, cudaStream_t s);
+
+// Algorithm 1 (ssm_admm.cu)
+ssm_status admm_tables(ssm_plan_s* pl, std::vector<std::pair<float**, std::vector<float>>>* out);
+int admm_partial_rows(const ssm_plan_s* pl);
+ssm_status admm_prepare();
+ssm_status admm_iteration(ssm_plan_s* pl, bool check, double* partial, int* nparts,
+                          cudaStream_t s);
 
 // tensor-core dense iteration (ssm_tc.cu)
 ssm_status tc_prepare(ssm_plan_s* pl, cudaStream_t s);

@@ -53,8 +53,8 @@ bool same_plan(const ssm_params& a, const ssm_params& b) {
     if (a.dims[d] != b.dims[d]) return false;
   const double xa = a.xi_p > 0 ? a.xi_p : 0.0, xb = b.xi_p > 0 ? b.xi_p : 0.0;
   const double ta = a.rank_tol > 0 ? a.rank_tol : 5e-5, tb = b.rank_tol > 0 ? b.rank_tol : 5e-5;
-  const int pa = a.form == SSM_FORM_DENSE ? a.precision : 0;
-  const int pb = b.form == SSM_FORM_DENSE ? b.precision : 0;
+  const int pa = a.form != SSM_FORM_LOWRANK ? a.precision : 0;
+  const int pb = b.form != SSM_FORM_LOWRANK ? b.precision : 0;
   const int ra = a.form == SSM_FORM_LOWRANK ? a.rank : 0;
   const int rb = b.form == SSM_FORM_LOWRANK ? b.rank : 0;
   return a.lambda == b.lambda && a.beta == b.beta && xa == xb && a.form == b.form && ra == rb &&

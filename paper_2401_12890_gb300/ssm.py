@@ -23,7 +23,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ssm.h")
 
 SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENAN, SSM_ETIMEOUT, SSM_EUNSUPPORTED, \
     SSM_ENOTCONVERGED, SSM_EPENDING = range(9)
-FORMS = {"lowrank": 0, "dense": 1}
+FORMS = {"lowrank": 0, "dense": 1, "admm": 2}
 PRECISIONS = {"fp32": 0, "bf16x3": 1}
 
 
