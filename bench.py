@@ -176,7 +176,7 @@ class Dist:
             self.pg.destroy_process_group()
 
 
-FORMS = [("lowrank", "fp32"), ("dense", "bf16x3"), ("dense", "fp32")]
+FORMS = [("lowrank", "fp32"), ("dense", "bf16x3"), ("dense", "fp32"), ("admm", "fp32")]
 
 
 def form_key(form, prec):
@@ -191,6 +191,8 @@ def dominant_kernel(form, prec, Q, N, r):
         return ("lowrank_iter_kernel", "ssm_lowrank.cu", "hbm",
                 8.0 * Q * N + 12.0 * r * N, "GB/s")
     if prec == "fp32":
+        # (for Algorithm 1 the profiled time is the whole iteration, of which the x-step
+        # product is this amount of work)
         return ("sgemm_kernel", "ssm_dense.cu", "alu", 2.0 * Q * Q * N, "TFLOP/s")
     return ("tc_gemm_kernel", "ssm_tc.cu", "tensor", 3 * 2.0 * Q * Q * N, "TFLOP/s")
 
@@ -282,10 +284,12 @@ def bench_ours(args):
                "main_kernel_ms_avg": kms / max(kl, 1), "main_kernel_launches": kl}
         # time to tolerance: fresh solves to ||z-f|| and ||dz|| <= TTT_TOL ||z||
         tplan = make_plan(form, prec, max_iter=20000, tol_primal=TTT_TOL, tol_change=TTT_TOL)
-        tplan.solve(Md, F)
         reps = args.ttt_repeats if (form, prec) == head else 3
-        if form == "dense" and prec == "fp32":
-            reps = 2
+        slow = prec == "fp32" and form != "lowrank"   # seconds per solve: one cold sample
+        if slow:
+            reps = 1
+        else:
+            tplan.solve(Md, F)
         times, iters = [], []
         for _ in range(reps):
             torch.cuda.synchronize()
@@ -294,11 +298,17 @@ def bench_ours(args):
             torch.cuda.synchronize()
             times.append(1e3 * (time.perf_counter() - t0))
             iters.append(tinfo["iterations"])
+        # the objective of Eq. 7 with the full K reached at the stop (the same measure for
+        # every form; the low-rank form solves the problem with K_r)
+        J_full = tplan.objective(Md, F, use_full_k=True)
         tplan.close()
         rec["time_to_tol_ms"] = {"tol": TTT_TOL, "p50": float(np.percentile(times, 50)),
                                  "p99": float(np.percentile(times, 99)),
                                  "iterations": int(statistics.median(iters)),
-                                 "samples": len(times)}
+                                 "samples": len(times), "objective_full_k": J_full,
+                                 "rule": ("||f-x||^2+||f-y||^2+||f-z||^2 and ||dy||^2 "
+                                          "relative to ||y||^2" if form == "admm" else
+                                          "||z-f|| and ||dz|| relative to ||z||")}
         results[key] = rec
         if (form, prec) == head:
             kname, kfile, bound, amount, unit = dominant_kernel(form, prec, Q, N, info["rank"])
@@ -391,15 +401,18 @@ def cpu_baseline_and_errors(K, M, w, Md, F, make_plan, forms):
                           f"{WORKLOAD} inputs, setup + {iters} iterations ({dt:.1f} s); "
                           "numpy's default BLAS threading"}
     errors = {}
-    refd = None
+    refd = refa = None
     for form, prec in forms:
         if form == "dense" and refd is None:
             refd = L.ladmm(K, M, w.dims, w.lam, w.beta, dense=True, iters=iters, check_every=0)
+        if form == "admm" and refa is None:
+            from oracle import admm as A
+            refa = A.admm(K, M, w.dims, w.lam, w.beta, iters=iters)
         pl = make_plan(form, prec, max_iter=iters, check_every=0)
         out, _ = pl.solve(Md, F)
         z = out.cpu().numpy().astype(np.float64)
         pl.close()
-        zr = (refd if form == "dense" else ref)["z"]
+        zr = refa["y"] if form == "admm" else (refd if form == "dense" else ref)["z"]
         errors[form_key(form, prec)] = {
             "iterations": iters,
             "rel_fro": float(np.linalg.norm(z - zr) / np.linalg.norm(zr))}
