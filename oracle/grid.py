@@ -11,6 +11,11 @@ boundary is free: voxels on the edge have fewer neighbours, there is no wrap-aro
 and no ghost voxel (the paper's maskless form, footnote to Algorithm 1).
 
 Voxel index n = x + nx*(y + ny*z).
+
+Masks: the paper's maskless form estimates only the voxels inside the object and
+imposes no smoothness across the object boundary (footnote to Algorithm 1). With a
+voxel mask (True = inside), the adjacent pairs are those with both voxels inside, i.e.
+the grid graph induced by the mask; voxels outside belong to no pair.
 """
 from __future__ import annotations
 
@@ -18,8 +23,9 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def neighbor_pairs(dims):
-    """All ordered pairs (n, m) with m adjacent to n, as two int64 arrays."""
+def neighbor_pairs(dims, mask=None):
+    """All ordered pairs (n, m) with m adjacent to n (both inside `mask` when given),
+    as two int64 arrays."""
     dims = tuple(int(d) for d in dims)
     N = int(np.prod(dims))
     idx = np.arange(N).reshape(tuple(reversed(dims)))  # [z][y][x] (x fastest)
@@ -35,15 +41,20 @@ def neighbor_pairs(dims):
         dst += [b, a]
     if not src:
         return np.zeros(0, np.int64), np.zeros(0, np.int64)
-    return np.concatenate(src), np.concatenate(dst)
+    n, m = np.concatenate(src), np.concatenate(dst)
+    if mask is not None:
+        inside = np.asarray(mask, bool).ravel()
+        keep = inside[n] & inside[m]
+        n, m = n[keep], m[keep]
+    return n, m
 
 
-def difference_operator(dims, pairs=2):
+def difference_operator(dims, pairs=2, mask=None):
     """Sparse D (rows = adjacent pairs, cols = N voxels) with (D f)_row = f_n - f_m.
 
     pairs=2: one row per ordered pair (literal Eq. 8). pairs=1: one row per edge.
     """
-    n, m = neighbor_pairs(dims)
+    n, m = neighbor_pairs(dims, mask)
     if pairs == 1:
         keep = n < m
         n, m = n[keep], m[keep]
@@ -57,9 +68,9 @@ def difference_operator(dims, pairs=2):
     return D
 
 
-def dtd(dims, pairs=2):
+def dtd(dims, pairs=2, mask=None):
     """D^T D as a sparse N x N matrix (symmetric)."""
-    D = difference_operator(dims, pairs)
+    D = difference_operator(dims, pairs, mask)
     return (D.T @ D).tocsr()
 
 
@@ -68,9 +79,9 @@ def apply_dtd(Z, DtD):
     return (DtD @ Z.T).T
 
 
-def roughness(Z, dims, pairs=2):
+def roughness(Z, dims, pairs=2, mask=None):
     """R(Z) = 1/2 ||D Z||^2 summed over all Q maps (Eq. 8)."""
-    D = difference_operator(dims, pairs)
+    D = difference_operator(dims, pairs, mask)
     DZ = D @ Z.T
     return 0.5 * float(np.sum(DZ * DZ))
 

@@ -76,21 +76,53 @@ def dense_inverse(K, beta):
 
 def ladmm(K, M, dims, lam, beta, *, rank=None, dense=False, xi_p=None, iters=300,
           tol_primal=0.0, tol_change=0.0, check_every=10, pairs=2, rank_tol=5e-5,
-          return_history=False):
+          return_history=False, mask=None):
     """Run Algorithm 2 (or its full-rank Eq. 26 variant with dense=True).
 
     rank: None -> the rank rule of Sec. III-E with `rank_tol`; int -> that r.
-    xi_p: None -> Eq. 32, 0.75 lambda ||D^T D|| + 1e-10.
+    xi_p: None -> Eq. 32, 0.75 lambda ||D^T D|| + 1e-10, with ||D^T D|| of the box grid
+    (with a mask this bounds the masked operator's norm from above: removing edges
+    from a graph cannot raise its Laplacian's eigenvalues).
+    mask: voxels inside the object (True); the problem is posed on them alone, with the
+    pairs of the induced grid graph, and z, f, d are 0 outside.
     Returns a dict with z, f, d (Q x N), iterations run, r, xi_p and the check history.
     """
+    if mask is not None:
+        inside = np.flatnonzero(np.asarray(mask, bool).ravel())
+        if xi_p is None:
+            xi_p = grid.xi_p_rule(lam, dims, pairs)
+        sub_dtd = grid.dtd(dims, pairs, mask)[inside][:, inside]
+        res = _ladmm_core(K, np.asarray(M, np.float64)[:, inside], sub_dtd, lam, beta,
+                          rank=rank, dense=dense, xi_p=xi_p, iters=iters,
+                          tol_primal=tol_primal, tol_change=tol_change,
+                          check_every=check_every, rank_tol=rank_tol)
+        for key in ("z", "f", "d"):
+            full = np.zeros((res[key].shape[0], int(np.prod(dims))))
+            full[:, inside] = res[key]
+            res[key] = full
+        if not return_history:
+            res.pop("history", None)
+        return res
+    if xi_p is None:
+        xi_p = grid.xi_p_rule(lam, dims, pairs)
+    K_ = np.asarray(K, np.float64)
+    assert np.asarray(M).shape[0] == K_.shape[0] and int(np.prod(dims)) == np.asarray(M).shape[1]
+    res = _ladmm_core(K, M, grid.dtd(dims, pairs), lam, beta, rank=rank, dense=dense,
+                      xi_p=xi_p, iters=iters, tol_primal=tol_primal, tol_change=tol_change,
+                      check_every=check_every, rank_tol=rank_tol)
+    if not return_history:
+        res.pop("history", None)
+    return res
+
+
+def _ladmm_core(K, M, DtD, lam, beta, *, rank, dense, xi_p, iters, tol_primal, tol_change,
+                check_every, rank_tol):
+    """Algorithm 2 on the voxels of M (columns) coupled by the given D^T D."""
     K = np.asarray(K, np.float64)
     M = np.asarray(M, np.float64)
     P, Q = K.shape
     N = M.shape[1]
-    assert M.shape[0] == P and int(np.prod(dims)) == N
-    if xi_p is None:
-        xi_p = grid.xi_p_rule(lam, dims, pairs)
-    DtD = grid.dtd(dims, pairs)
+    assert M.shape[0] == P and DtD.shape == (N, N)
 
     if dense:
         # Eq. 26 with the unapproximated K: g_n = K^T m_n, M_mat = (K^T K + beta I)^-1
@@ -133,18 +165,18 @@ def ladmm(K, M, dims, lam, beta, *, rank=None, dense=False, xi_p=None, iters=300
             used = [(t, v) for t, v in ((tol_primal, rp), (tol_change, rc)) if t > 0]
             if used and all(v <= t for t, v in used):
                 break
-    out = {"z": z, "f": f, "d": d, "iters": k, "r": r, "xi_p": xi_p}
-    if return_history:
-        out["history"] = history
-    return out
+    return {"z": z, "f": f, "d": d, "iters": k, "r": r, "xi_p": xi_p, "history": history}
 
 
-def objective(K, M, Z, dims, lam, pairs=2):
-    """Eq. 7 with Eq. 8: 1/2 ||M - K Z||_F^2 + lambda * 1/2 ||D Z||^2."""
+def objective(K, M, Z, dims, lam, pairs=2, mask=None):
+    """Eq. 7 with Eq. 8: 1/2 ||M - K Z||_F^2 + lambda * 1/2 ||D Z||^2 (over the voxels
+    inside `mask` and the pairs of its induced grid graph when a mask is given)."""
     K = np.asarray(K, np.float64)
     R = np.asarray(M, np.float64) - K @ np.asarray(Z, np.float64)
+    if mask is not None:
+        R = R[:, np.asarray(mask, bool).ravel()]
     return 0.5 * float(np.sum(R * R)) + lam * grid.roughness(np.asarray(Z, np.float64),
-                                                             dims, pairs)
+                                                             dims, pairs, mask)
 
 
 def truncated_dictionary(K, r):
