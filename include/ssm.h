@@ -225,6 +225,22 @@ ssm_status ssm_profile_read(ssm_plan_t plan, double* main_kernel_ms,
 ssm_status ssm_plan_set_graphs(ssm_plan_t plan, int enable);
 
 /*
+ * Restrict the problem to the voxels inside an object: mask_host holds N bytes (voxel
+ * order as M's columns), nonzero = inside; NULL removes the mask. This is the paper's
+ * maskless form (footnote to Algorithm 1): only voxels inside the object are estimated
+ * and no smoothness is imposed across the object boundary, i.e. D of Eq. 8 has the
+ * pairs of the grid graph the mask induces (an inside voxel's neighbours outside the
+ * object do not count). Later solves return F = 0 outside the object, and ssm_objective
+ * sums the data term over the inside voxels and the roughness over the induced pairs.
+ * xi_p (Eq. 32) keeps the box grid's ||D^T D||, an upper bound of the masked operator's
+ * norm (removing edges cannot raise a graph Laplacian's eigenvalues). The plan copies the
+ * mask to the device (N more bytes, not in ssm_plan_footprint) and drops its captured
+ * graphs; synchronises `stream`. The ADMM form does not support masks
+ * (SSM_EUNSUPPORTED).
+ */
+ssm_status ssm_plan_set_mask(ssm_plan_t plan, const uint8_t* mask_host, void* stream);
+
+/*
  * Change the plan's beta without refactorising K (the spectral factors of Sec. III-D do
  * not depend on beta): re-forms the weights of Eq. 28 (low-rank) or the inverse of
  * Eq. 26 (dense) on `stream` and drops the plan's captured graphs. The next solve uses

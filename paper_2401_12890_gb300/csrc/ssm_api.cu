@@ -192,6 +192,7 @@ void release(ssm_plan_s* pl) {
     dfree(*v);
   for (auto& tt : pl->adm_T)
     for (float*& v : tt) dfree(v);
+  dfree(pl->mask);
   dfree(pl->C32);
   dfree(pl->S);
   dfree(pl->H);
@@ -669,8 +670,18 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
     for (float* v : {a.x, a.y, a.z, a.dx, a.dy, a.dz})
       SSM_CUDA(cudaMemsetAsync(v, 0, sizeof(float) * QN, s));
   } else {
-    SSM_CUDA(cudaMemsetAsync(pl->Z[0], 0, sizeof(float) * QN, s));
-    SSM_CUDA(cudaMemsetAsync(pl->Dl[0], 0, sizeof(float) * QN, s));
+    // with a mask, voxels outside the object are never written: both ping-pong halves
+    // (and both tensor-core operands) must hold zeros there
+    const int nbuf = pl->mask ? 2 : 1;
+    for (int i = 0; i < nbuf; ++i) {
+      SSM_CUDA(cudaMemsetAsync(pl->Z[i], 0, sizeof(float) * QN, s));
+      SSM_CUDA(cudaMemsetAsync(pl->Dl[i], 0, sizeof(float) * QN, s));
+    }
+    if (pl->mask && pl->Whi[1]) {
+      const size_t WN = (size_t)pl->g.ld * pl->Qp;
+      SSM_CUDA(cudaMemsetAsync(pl->Whi[1], 0, sizeof(__nv_bfloat16) * WN, s));
+      SSM_CUDA(cudaMemsetAsync(pl->Wlo[1], 0, sizeof(__nv_bfloat16) * WN, s));
+    }
   }
 
   const bool use_tol = p.tol_primal > 0 || p.tol_change > 0;
@@ -907,6 +918,35 @@ ssm_status ssm_plan_set_graphs(ssm_plan_t plan, int enable) {
     return SSM_EINVAL;
   }
   plan->use_graphs = enable != 0;
+  return SSM_OK;
+}
+
+ssm_status ssm_plan_set_mask(ssm_plan_t plan, const uint8_t* mask_host, void* stream) {
+  if (!plan) {
+    set_error("NULL plan");
+    return SSM_EINVAL;
+  }
+  if (plan->p.form == SSM_FORM_ADMM) {
+    set_error("the ADMM form's z-step needs the whole box grid: masks are not supported");
+    return SSM_EUNSUPPORTED;
+  }
+  SSM_CUDA(cudaSetDevice(plan->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // captured graphs hold the old mask pointer (or none) in their kernel arguments
+  for (GraphBlock& b : plan->graphs)
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+  plan->graphs.clear();
+  if (!mask_host) {
+    if (plan->mask) {
+      SSM_CUDA(cudaStreamSynchronize(s));
+      dfree(plan->mask);
+      plan->bytes -= plan->g.N;
+    }
+    return SSM_OK;
+  }
+  if (!plan->mask) SSM_TRY(palloc(plan, &plan->mask, (size_t)plan->g.N, s));
+  SSM_CUDA(cudaMemcpyAsync(plan->mask, mask_host, (size_t)plan->g.N, cudaMemcpyHostToDevice, s));
+  SSM_CUDA(cudaStreamSynchronize(s));   // the caller may free its buffer on return
   return SSM_OK;
 }
 

@@ -111,6 +111,7 @@ struct UpdateArgs {
   __nv_bfloat16* __restrict__ Whi;   // optional BF16 split of w'
   __nv_bfloat16* __restrict__ Wlo;
   double* __restrict__ partial;
+  const uint8_t* __restrict__ mask;  // voxels inside the object (nullptr: every voxel)
   Grid g;
   int Q;
   float beta, xi, lam_s, inv_xb;
@@ -119,7 +120,8 @@ struct UpdateArgs {
 template <bool CHECK>
 __global__ void __launch_bounds__(UV) dense_update_kernel(UpdateArgs a) {
   const int64_t n = (int64_t)blockIdx.x * UV + threadIdx.x;
-  const bool valid = n < a.g.N;
+  const uint8_t* mk = a.mask;
+  const bool valid = n < a.g.N && (!mk || mk[n]);   // outside the object: left alone
   const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
   const int64_t sy = nx, sz = (int64_t)nx * ny, ld = a.g.ld;
   int x = 0, y = 0, zc = 0;
@@ -129,8 +131,13 @@ __global__ void __launch_bounds__(UV) dense_update_kernel(UpdateArgs a) {
     y = (int)(t % ny);
     zc = (int)(t / ny);
   }
-  const bool hxm = x > 0, hxp = x < nx - 1, hym = y > 0, hyp = y < ny - 1;
-  const bool hzm = zc > 0, hzp = zc < nz - 1;
+  const int64_t sy_ = nx, sz_ = (int64_t)nx * ny;
+  const bool hxm = valid && x > 0 && (!mk || mk[n - 1]);
+  const bool hxp = valid && x < nx - 1 && (!mk || mk[n + 1]);
+  const bool hym = valid && y > 0 && (!mk || mk[n - sy_]);
+  const bool hyp = valid && y < ny - 1 && (!mk || mk[n + sy_]);
+  const bool hzm = valid && zc > 0 && (!mk || mk[n - sz_]);
+  const bool hzp = valid && zc < nz - 1 && (!mk || mk[n + sz_]);
   const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
   float s1 = 0.f, s2 = 0.f, s3 = 0.f;
   const int q0 = blockIdx.y * UQ, q1 = min(a.Q, q0 + UQ);
@@ -211,10 +218,13 @@ __global__ void finish_kernel(const double* __restrict__ part, int nparts, int w
 // neighbour pair and every map of (F_n - F_m)^2 (the forward differences)
 __global__ void __launch_bounds__(UV) objective_kernel(const float* __restrict__ Res, int P,
                                                        const float* __restrict__ F, int64_t ldf,
-                                                       int Q, Grid g, double* __restrict__ part) {
+                                                       int Q, Grid g,
+                                                       const uint8_t* __restrict__ mk,
+                                                       double* __restrict__ part) {
   const int64_t n = (int64_t)blockIdx.x * UV + threadIdx.x;
   double r2 = 0.0, e2 = 0.0;
-  if (n < g.N) {
+  // with a mask: the data term over the voxels inside, the pairs with both ends inside
+  if (n < g.N && (!mk || mk[n])) {
     for (int p = 0; p < P; ++p) {
       const float r = Res[(int64_t)p * g.ld + n];
       r2 += (double)r * r;
@@ -227,9 +237,18 @@ __global__ void __launch_bounds__(UV) objective_kernel(const float* __restrict__
       const float* row = F + (int64_t)q * ldf;
       const float v = row[n];
       float acc = 0.f;
-      if (x + 1 < g.nx) { const float dd = v - row[n + 1]; acc = fmaf(dd, dd, acc); }
-      if (y + 1 < g.ny) { const float dd = v - row[n + sy]; acc = fmaf(dd, dd, acc); }
-      if (z + 1 < g.nz) { const float dd = v - row[n + sz]; acc = fmaf(dd, dd, acc); }
+      if (x + 1 < g.nx && (!mk || mk[n + 1])) {
+        const float dd = v - row[n + 1];
+        acc = fmaf(dd, dd, acc);
+      }
+      if (y + 1 < g.ny && (!mk || mk[n + sy])) {
+        const float dd = v - row[n + sy];
+        acc = fmaf(dd, dd, acc);
+      }
+      if (z + 1 < g.nz && (!mk || mk[n + sz])) {
+        const float dd = v - row[n + sz];
+        acc = fmaf(dd, dd, acc);
+      }
       e2 += acc;
     }
   }
@@ -278,6 +297,7 @@ ssm_status dense_update(ssm_plan_s* pl, int cur, const float* acc, bool check, b
   a.Whi = write_bf16_w ? pl->Whi[cur ^ 1] : nullptr;
   a.Wlo = write_bf16_w ? pl->Wlo[cur ^ 1] : nullptr;
   a.partial = partial;
+  a.mask = pl->mask;
   a.g = pl->g;
   a.Q = pl->Q;
   a.beta = (float)pl->p.beta;
@@ -304,7 +324,7 @@ ssm_status finish_partials(const double* partial, int nparts, int width, double*
 ssm_status objective_terms(const ssm_plan_s* pl, const float* Res, int P, const float* F,
                            int64_t ldf, double* partial, int* nparts, cudaStream_t s) {
   const unsigned nb = (unsigned)((pl->g.N + UV - 1) / UV);
-  objective_kernel<<<nb, UV, 0, s>>>(Res, P, F, ldf, pl->Q, pl->g, partial);
+  objective_kernel<<<nb, UV, 0, s>>>(Res, P, F, ldf, pl->Q, pl->g, pl->mask, partial);
   SSM_LAUNCHED();
   *nparts = (int)nb;
   return SSM_OK;

@@ -155,6 +155,8 @@ struct ssm_plan_s {
   ssm::AdmmState adm{};
   float* adm_T[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   float* adm_D = nullptr;
+  // voxels inside the object (N bytes, 1 = inside), nullptr = every voxel
+  uint8_t* mask = nullptr;
   // iteration blocks replayed as CUDA graphs (ssm_plan_set_graphs)
   bool use_graphs = false;
   std::vector<ssm::GraphBlock> graphs;

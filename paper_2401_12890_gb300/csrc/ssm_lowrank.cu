@@ -72,6 +72,7 @@ struct LowrankArgs {
   const float* __restrict__ coefA;  // R
   const float* __restrict__ coefW;  // R
   double* __restrict__ partial;     // 4 doubles per block (check iterations)
+  const uint8_t* __restrict__ mask; // voxels inside the object (nullptr: every voxel)
   int* __restrict__ err;            // device error word (SSM_ETIMEOUT on a failed wait)
   Grid g;
   int Q;
@@ -199,9 +200,16 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
         y = (int)(t % ny);
         zc = (int)(t / ny);
       }
-      const bool hxm = valid && x > 0, hxp = valid && x < nx - 1;
-      const bool hym = valid && y > 0, hyp = valid && y < ny - 1;
-      const bool hzm = valid && zc > 0, hzp = valid && zc < nz - 1;
+      // a voxel outside the object is left alone (its z stays 0) and is nobody's
+      // neighbour: the grid graph is the one the mask induces
+      const uint8_t* mk = a.mask;
+      const bool in = valid && (!mk || mk[n]);
+      const bool hxm = in && x > 0 && (!mk || mk[n - 1]);
+      const bool hxp = in && x < nx - 1 && (!mk || mk[n + 1]);
+      const bool hym = in && y > 0 && (!mk || mk[n - nx]);
+      const bool hyp = in && y < ny - 1 && (!mk || mk[n + nx]);
+      const bool hzm = in && zc > 0 && (!mk || mk[n - plane]);
+      const bool hzp = in && zc < nz - 1 && (!mk || mk[n + plane]);
       const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
       const float e1 = (a.xi + a.beta - a.lam_s * deg) * a.inv_xb;   // weight of z
       int nidx[4];
@@ -223,7 +231,7 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
 #pragma unroll
       for (int i = 0; i < R / 2; ++i) {
         float a0 = 0.f, a1 = 0.f;
-        if (valid) {
+        if (in) {
           float u0 = 0.f, u1 = 0.f;
           const float* pt = a.Pin + (tile * a.maxseg) * (int64_t)(R * TV);
           for (int sg = 0; sg < nseg; ++sg) {
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
         const float* ddr = reinterpret_cast<const float*>(st + L.dd);
         const float* vvr = reinterpret_cast<const float*>(st + L.vv);
         const int qn = min(QC, qend - qc0);
-        if (!failed && valid) {
+        if (!failed && in) {
 #pragma unroll 2
           for (int row = 0; row < qn; ++row) {
             const float z = zcr[row * ZW + 4 + v];
@@ -297,8 +305,8 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
       float* po = a.Pout + ((tile * a.maxseg + sidx) * (int64_t)R) * TV;
 #pragma unroll
       for (int i = 0; i < R / 2; ++i) {
-        po[(2 * i) * TV + v] = valid ? uacc[i].x : 0.f;
-        po[(2 * i + 1) * TV + v] = valid ? uacc[i].y : 0.f;
+        po[(2 * i) * TV + v] = in ? uacc[i].x : 0.f;
+        po[(2 * i + 1) * TV + v] = in ? uacc[i].y : 0.f;
       }
       r = tile * Q + qend;
     }
@@ -437,6 +445,7 @@ ssm_status lowrank_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, 
   a.coefA = pl->coefA;
   a.coefW = pl->coefW;
   a.partial = partial;
+  a.mask = pl->mask;
   a.err = pl->dev_err;
   a.g = pl->g;
   a.Q = pl->Q;

@@ -50,6 +50,7 @@ struct UpdArgs {
   __nv_bfloat16* __restrict__ Whi;
   __nv_bfloat16* __restrict__ Wlo;
   double* __restrict__ partial;
+  const uint8_t* __restrict__ mask;   // voxels inside the object (nullptr: every voxel)
   int* __restrict__ err;
   Grid g;
   int Q, Qp, nqc;              // nqc = chunks per tile
@@ -146,9 +147,15 @@ __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
         y = (int)(t % ny);
         zc = (int)(t / ny);
       }
-      const bool hxm = valid && x > 0, hxp = valid && x < nx - 1;
-      const bool hym = valid && y > 0, hyp = valid && y < ny - 1;
-      const bool hzm = valid && zc > 0, hzp = valid && zc < nz - 1;
+      // a voxel outside the object is left alone and is nobody's neighbour
+      const uint8_t* mk = a.mask;
+      const bool in = valid && (!mk || mk[n]);
+      const bool hxm = in && x > 0 && (!mk || mk[n - 1]);
+      const bool hxp = in && x < nx - 1 && (!mk || mk[n + 1]);
+      const bool hym = in && y > 0 && (!mk || mk[n - nx]);
+      const bool hyp = in && y < ny - 1 && (!mk || mk[n + nx]);
+      const bool hzm = in && zc > 0 && (!mk || mk[n - plane]);
+      const bool hzp = in && zc < nz - 1 && (!mk || mk[n + plane]);
       const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
       const bool flags[4] = {ny > 1 ? hym : hzm, ny > 1 ? hyp : hzp, hzm, hzp};
       int nidx[4];
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
       for (int rr = 0; rr < UQH; ++rr) {
         wv[rr] = 0.f;
         const int r = qh + rr, q = q0 + rr;
-        if (valid && q < a.Q) {
+        if (in && q < a.Q) {
           const float z = zr[r * UZW + 4 + v], d = dr[r * UTV + v];
           float nb = 0.f;
           if (hxm) nb += zr[r * UZW + 3 + v];
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
-      if (valid) {
+      if (in) {
         // UQH values = a part (a half or a quarter) of the voxel's 32-byte sector in hi
         // and in lo
         uint32_t hh[UQH / 2], ll[UQH / 2];
@@ -297,6 +304,7 @@ ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* 
   a.Whi = pl->Whi[cur ^ 1];
   a.Wlo = pl->Wlo[cur ^ 1];
   a.partial = partial;
+  a.mask = pl->mask;
   a.err = pl->dev_err;
   a.g = pl->g;
   a.Q = pl->Q;

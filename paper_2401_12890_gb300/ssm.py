@@ -145,6 +145,7 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_plan_set_graphs.argtypes = [vp, ctypes.c_int]
     lib.ssm_plan_launch_info.argtypes = [vp, ctypes.POINTER(SsmLaunchInfo)]
     lib.ssm_plan_set_beta.argtypes = [vp, ctypes.c_double, vp]
+    lib.ssm_plan_set_mask.argtypes = [vp, vp, vp]
     lib.ssm_tune_beta.argtypes = [ctypes.POINTER(SsmParams), vp, vp, i64, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   vp, dp, vp, vp]
@@ -167,7 +168,7 @@ def load_library(path: str = LIB_PATH):
                  "ssm_objective", "ssm_plan_factors", "ssm_destroy", "ssm_profile_enable",
                  "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
                  "ssm_plan_ex", "ssm_server_submit_device", "ssm_plan_set_beta",
-                 "ssm_tune_beta", "ssm_plan_launch_info",
+                 "ssm_tune_beta", "ssm_plan_launch_info", "ssm_plan_set_mask",
                  "ssm_plan_footprint", "ssm_plan_device_bytes", "ssm_server_default_config",
                  "ssm_server_create", "ssm_server_submit", "ssm_server_poll", "ssm_server_wait",
                  "ssm_server_stats_read", "ssm_server_destroy"):
@@ -267,6 +268,19 @@ class Plan:
                              _stream_handle(stream), int(launch_waves))
         if st != SSM_OK:
             raise SsmError(st, "ssm_plan")
+
+    def set_mask(self, mask, stream=None):
+        """Estimate only the voxels where `mask` (N values, voxel order) is nonzero
+        (ssm_plan_set_mask); None removes the mask."""
+        if mask is None:
+            ptr = None
+        else:
+            m = np.ascontiguousarray(np.asarray(mask).ravel() != 0, dtype=np.uint8)
+            assert m.size == self.N
+            ptr = m.ctypes.data_as(ctypes.c_void_p)
+        st = load_library().ssm_plan_set_mask(self._h, ptr, _stream_handle(stream))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_plan_set_mask")
 
     def set_beta(self, beta, stream=None):
         """Change beta without refactorising K (ssm_plan_set_beta)."""
