@@ -95,6 +95,22 @@ def _smooth_field(rng, dims, n_waves=4):
     return np.ascontiguousarray(field.transpose(tuple(reversed(range(len(dims)))))).ravel()
 
 
+def multi_echo_t2_dictionary(te_ms, t2_ms):
+    """Multi-echo spin-echo T2 relaxometry (a 1D spectrum): K[p, q] = exp(-TE_p / T2_q)."""
+    te = np.asarray(te_ms, np.float64)[:, None]
+    t2 = np.asarray(t2_ms, np.float64)[None, :]
+    return np.exp(-te / t2)
+
+
+def ellipse_mask(dims, fill):
+    """A 2D object mask, voxel order: the ellipse inscribed in `fill` of the grid."""
+    nx, ny = dims
+    x = (np.arange(nx) + 0.5) / nx - 0.5
+    y = (np.arange(ny) + 0.5) / ny - 0.5
+    X, Y = np.meshgrid(x, y, indexing="xy")          # [y][x]
+    return ((X / (0.5 * fill)) ** 2 + (Y / (0.5 * fill)) ** 2 <= 1.0).ravel()
+
+
 def spectral_peaks(shape2d, centers, widths):
     """Unit-sum Gaussian peaks on a 2D spectral grid in normalised log coordinates.
 
@@ -140,6 +156,8 @@ WORKLOADS = {
                           0.47668520453230206, 300, 100.0, 44),
     "mrf2d": Workload("mrf2d", (192, 192), 1000, 900, 1e-2,
                       0.025222210292153446, 300, 50.0, 45),
+    "mse_t2": Workload("mse_t2", (84, 72), 32, 300, 1e-2,
+                       0.02809082955801525, 300, 100.0, 47),
 }
 
 
@@ -160,12 +178,24 @@ def dictionary_for(name: str) -> np.ndarray:
     if name == "mrf2d":
         return spgr_fingerprint_dictionary(
             1000, np.geomspace(200, 4000, 30), np.geomspace(10, 300, 30), seed=1045)
+    if name == "mse_t2":
+        # 32 echoes every 10 ms, 300 log-spaced T2 values (a 1D spectrum per voxel)
+        return multi_echo_t2_dictionary(np.arange(1, 33) * 10.0, np.geomspace(10, 2000, 300))
     raise KeyError(name)
+
+
+def mask_for(name: str, dims=None):
+    """The object mask of a named workload (None: every voxel is estimated). The
+    1D-spectrum workload's object is an ellipse of 4472 voxels in an 84 x 72 grid, about
+    the voxel count of the paper's multicomponent T2 brain data set (Sec. IV-C)."""
+    if name == "mse_t2":
+        return ellipse_mask(dims or WORKLOADS[name].dims, fill=0.9695)
+    return None
 
 
 def _spectral_shape(name):
     return {"dr2d_tiny": (15, 15), "dr2d_slice": (50, 50),
-            "rr3d_t1t2": (40, 40), "mrf2d": (30, 30)}[name]
+            "rr3d_t1t2": (40, 40), "mrf2d": (30, 30), "mse_t2": (300, 1)}[name]
 
 
 def ground_truth_factors(dims, spec_shape, seed, n_peaks=3):
@@ -201,6 +231,9 @@ def make_problem(name: str, dims=None, seed=None, snr=None, dtype=np.float32):
     snr = w.snr if snr is None else snr
     K = dictionary_for(name)
     S, A = ground_truth_factors(dims, _spectral_shape(name), seed)
+    mask = mask_for(name, dims)
+    if mask is not None:
+        A = A * mask[None, :]       # nothing outside the object: its data is noise alone
     KS = K @ S                      # P x J
     rng = np.random.default_rng(seed + 1000)
     M = np.empty((K.shape[0], A.shape[1]), dtype=dtype)
