@@ -77,7 +77,7 @@ __host__ __device__ __forceinline__ int64_t ufloor4(int64_t v) {
   return v >= 0 ? (v & ~(int64_t)3) : -(((-v) + 3) & ~(int64_t)3);
 }
 
-template <bool CHECK, int UNCW>
+template <bool CHECK, int UNCW, bool MASKED>
 __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
     const __grid_constant__ UpdMaps maps, const UpdArgs a) {
   constexpr int UQH = UWarps<UNCW>::QH, UNT = UWarps<UNCW>::NT;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
         zc = (int)(t / ny);
       }
       // a voxel outside the object is left alone and is nobody's neighbour
-      const uint8_t* mk = a.mask;
+      const uint8_t* mk = MASKED ? a.mask : nullptr;   // unmasked: the checks fold away
       const bool in = valid && (!mk || mk[n]);
       const bool hxm = in && x > 0 && (!mk || mk[n - 1]);
       const bool hxp = in && x < nx - 1 && (!mk || mk[n + 1]);
@@ -250,12 +250,13 @@ template <int NCW>
 int update_per_sm(int nr) {
   const size_t shm = (size_t)ULayout(nr).total + 128;
   const size_t shm_max = (size_t)ULayout(4).total + 128;
-  cudaFuncSetAttribute(tc_update_kernel<true, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)shm_max);
-  cudaFuncSetAttribute(tc_update_kernel<false, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)shm_max);
+  for (const void* k : {(const void*)tc_update_kernel<true, NCW, false>,
+                        (const void*)tc_update_kernel<false, NCW, false>,
+                        (const void*)tc_update_kernel<true, NCW, true>,
+                        (const void*)tc_update_kernel<false, NCW, true>})
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_max);
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_update_kernel<true, NCW>,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_update_kernel<true, NCW, false>,
                                                 UWarps<NCW>::NT, shm);
   return std::max(1, b);
 }
@@ -319,17 +320,22 @@ ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* 
   const int grid = update_grid_impl(pl);
   *nparts = grid;
   const size_t shm = (size_t)ULayout(update_nr(pl)).total + 128;
+  const bool masked = pl->mask != nullptr;
+#define SSM_UPD(C, W, MK) tc_update_kernel<C, W, MK><<<grid, UWarps<W>::NT, shm, s>>>(m, a)
   if (update_ncw(pl) == 16) {
-    if (check)
-      tc_update_kernel<true, 16><<<grid, UWarps<16>::NT, shm, s>>>(m, a);
-    else
-      tc_update_kernel<false, 16><<<grid, UWarps<16>::NT, shm, s>>>(m, a);
+    if (masked) {
+      if (check) SSM_UPD(true, 16, true); else SSM_UPD(false, 16, true);
+    } else {
+      if (check) SSM_UPD(true, 16, false); else SSM_UPD(false, 16, false);
+    }
   } else {
-    if (check)
-      tc_update_kernel<true, 8><<<grid, UWarps<8>::NT, shm, s>>>(m, a);
-    else
-      tc_update_kernel<false, 8><<<grid, UWarps<8>::NT, shm, s>>>(m, a);
+    if (masked) {
+      if (check) SSM_UPD(true, 8, true); else SSM_UPD(false, 8, true);
+    } else {
+      if (check) SSM_UPD(true, 8, false); else SSM_UPD(false, 8, false);
+    }
   }
+#undef SSM_UPD
   SSM_LAUNCHED();
   return SSM_OK;
 }
