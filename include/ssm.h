@@ -408,6 +408,16 @@ ssm_status ssm_server_stats_read(ssm_server_t s, ssm_server_stats* out);
  * Tickets not yet collected become invalid. NULL is accepted. */
 ssm_status ssm_server_destroy(ssm_server_t s);
 
+/*
+ * Self-test of failure detection (no counterpart in the paper): every mbarrier wait in
+ * the solver's kernels is bounded and reports SSM_ETIMEOUT instead of hanging. This runs
+ * one small kernel whose wait can never succeed (an mbarrier nobody arrives at), polled
+ * `polls` times (1 .. 2^20) by the same wait routine, and returns the status the host
+ * reads back: SSM_ETIMEOUT when the mechanism works. The device stays usable afterwards.
+ * Synchronises `stream`.
+ */
+ssm_status ssm_selftest_wait_timeout(unsigned polls, void* stream);
+
 /* Static description of a status code. */
 const char* ssm_status_string(int status);
 

@@ -146,6 +146,7 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_plan_launch_info.argtypes = [vp, ctypes.POINTER(SsmLaunchInfo)]
     lib.ssm_plan_set_beta.argtypes = [vp, ctypes.c_double, vp]
     lib.ssm_plan_set_mask.argtypes = [vp, vp, vp]
+    lib.ssm_selftest_wait_timeout.argtypes = [ctypes.c_uint, vp]
     lib.ssm_tune_beta.argtypes = [ctypes.POINTER(SsmParams), vp, vp, i64, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   vp, dp, vp, vp]
@@ -169,6 +170,7 @@ def load_library(path: str = LIB_PATH):
                  "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
                  "ssm_plan_ex", "ssm_server_submit_device", "ssm_plan_set_beta",
                  "ssm_tune_beta", "ssm_plan_launch_info", "ssm_plan_set_mask",
+                 "ssm_selftest_wait_timeout",
                  "ssm_plan_footprint", "ssm_plan_device_bytes", "ssm_server_default_config",
                  "ssm_server_create", "ssm_server_submit", "ssm_server_poll", "ssm_server_wait",
                  "ssm_server_stats_read", "ssm_server_destroy"):

@@ -92,3 +92,8 @@ def test_null_arguments_rejected(lib):
     assert lib.ssm_solve(None, None, 0, None, 0, None, None) == ssm.SSM_EINVAL
     J = ctypes.c_double()
     assert lib.ssm_objective(None, None, 0, None, 0, 0, ctypes.byref(J), None) == ssm.SSM_EINVAL
+
+
+def test_selftest_rejects_bad_poll_counts_before_any_gpu_call(lib):
+    assert lib.ssm_selftest_wait_timeout(0, None) == ssm.SSM_EINVAL
+    assert lib.ssm_selftest_wait_timeout((1 << 20) + 1, None) == ssm.SSM_EINVAL
