@@ -258,8 +258,9 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
         const float* vvr = reinterpret_cast<const float*>(st + L.vv);
         const int qn = min(QC, qend - qc0);
         if (!failed && in) {
-#pragma unroll 2
-          for (int row = 0; row < qn; ++row) {
+#pragma unroll
+          for (int row = 0; row < QC; ++row) {
+            if (row >= qn) break;
             const float z = zcr[row * ZW + 4 + v];
             float nb = 0.f;
             if (hxm) nb += zcr[row * ZW + 3 + v];
