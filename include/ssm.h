@@ -138,6 +138,20 @@ ssm_status ssm_plan_ex(ssm_plan_t* out, const ssm_params* p, const double* K_hos
                        int device, void* stream, int launch_waves);
 
 /*
+ * A batch of nbatch independent problems that share the dictionary, the grid (p: one 1D
+ * or 2D slice), lambda, beta and the stopping rule -- e.g. the slices of one subject -- as
+ * one plan whose kernels solve them all at once (batching, no counterpart in the paper).
+ * The plan's grid is (nx, ny, nbatch) with no smoothness across the batch axis: each
+ * slice's problem is exactly Eq. 7 on its own grid, and xi_p (Eq. 32) is the slice's.
+ * M and F hold the slices one after another: P x (N nbatch), slice b in columns
+ * [b N, (b + 1) N). The residual test is over the whole batch (the batch stops when the
+ * stacked residuals meet the tolerance). Masks apply (N nbatch bytes). launch_waves as
+ * in ssm_plan_ex.
+ */
+ssm_status ssm_plan_batched(ssm_plan_t* out, const ssm_params* p, int64_t nbatch,
+                            const double* K_host, int device, void* stream, int launch_waves);
+
+/*
  * Run the LADMM iteration (Algorithm 2, steps 4-12) on data M and write F = z.
  *   M_dev : P x N floats on the device, leading dimension ldm >= N; read only.
  *   F_dev : Q x N floats on the device, leading dimension ldf >= N; written.

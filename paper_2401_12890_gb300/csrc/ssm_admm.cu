@@ -261,8 +261,9 @@ ssm_status admm_tables(ssm_plan_s* pl, std::vector<std::pair<float**, std::vecto
   for (int d = 0; d < 3; ++d) {
     const int n = (int)dims[d];
     mu[d].resize(n);
-    for (int k = 0; k < n; ++k) mu[d][k] = 2.0 - 2.0 * std::cos(M_PI * k / n);
-    if (n == 1) continue;
+    const bool linked = d < 2 || pl->g.zlink;
+    for (int k = 0; k < n; ++k) mu[d][k] = linked ? 2.0 - 2.0 * std::cos(M_PI * k / n) : 0.0;
+    if (n == 1 || !linked) continue;
     if (n > 256) {
       set_error("ADMM form: grid axes longer than 256 are not supported");
       return SSM_EUNSUPPORTED;
@@ -327,7 +328,7 @@ ssm_status admm_iteration(ssm_plan_s* pl, bool check, double* partial, int* npar
   const int64_t dims[3] = {pl->g.nx, pl->g.ny, pl->g.nz};
   int axes[3], na = 0;
   for (int d = 0; d < 3; ++d)
-    if (dims[d] > 1) axes[na++] = d;
+    if (dims[d] > 1 && (d < 2 || pl->g.zlink)) axes[na++] = d;   // a slice stack: no z step
   if (na == 0) {
     // one voxel: D^T D = 0, z = r / beta
     SSM_CUDA(cudaMemcpyAsync(st.z, st.r, sizeof(float) * (size_t)pl->Q * pl->g.ld,

@@ -226,7 +226,8 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   pl->g.nz = p.ndim >= 3 ? (int)p.dims[2] : 1;
   pl->g.N = (int64_t)pl->g.nx * pl->g.ny * pl->g.nz;
   pl->g.ld = round_up(pl->g.N, 128);
-  pl->dtd_norm = dtd_norm_closed(p.dims, p.ndim, p.stencil_pairs);
+  // a slice stack (z not linked) has the smoothness of one slice: the x and y axes only
+  pl->dtd_norm = dtd_norm_closed(p.dims, pl->g.zlink ? p.ndim : 2, p.stencil_pairs);
   pl->xi = p.xi_p > 0.0 ? p.xi_p : 0.75 * p.lambda * pl->dtd_norm + 1e-10;  // Eq. 32
   pl->lam_s = p.lambda * (p.stencil_pairs == 2 ? 2.0 : 1.0);
   pl->n = std::min(P, Q);
@@ -392,9 +393,10 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
 // rank is known only after the eigendecomposition: without a fixed rank the bound
 // takes r = min(P, Q, 64), the largest the low-rank kernel supports.
 ssm_status footprint_impl(const ssm_params& p, bool staging, int waves, int64_t* persistent,
-                          int64_t* peak) {
+                          int64_t* peak, bool zlink = true) {
   ssm_plan_s t;
   t.p = p;
+  t.g.zlink = zlink ? 1 : 0;
   t.waves = std::max(1, waves);
   t.P = p.P;
   t.Q = p.Q;
@@ -440,7 +442,8 @@ ssm_status footprint_impl(const ssm_params& p, bool staging, int waves, int64_t*
     add(4, 2 * QN);                           // H, Acc
     const int64_t dd[3] = {t.g.nx, t.g.ny, t.g.nz};
     for (int d = 0; d < 3; ++d)
-      if (dd[d] > 1) add(4, 2 * dd[d] * 64 * ((dd[d] + 63) / 64));  // DCT tables
+      if (dd[d] > 1 && (d < 2 || zlink))
+        add(4, 2 * dd[d] * 64 * ((dd[d] + 63) / 64));  // DCT tables
     add(4, t.g.N);                            // spectral scaling
     maxparts = std::max<int64_t>(admm_partial_rows(&t), dense_max_partials(&t));
   } else if (p.form == SSM_FORM_LOWRANK) {
@@ -755,7 +758,7 @@ ssm_status plan_footprint(const ssm_params& p, bool staging, int waves, int64_t*
 ssm_status validate_params(const ssm_params* p) { return validate(p); }
 
 ssm_status plan_create(ssm_plan_t* out, const ssm_params* p, const double* K_host, int device,
-                       cudaStream_t s, int waves) {
+                       cudaStream_t s, int waves, bool zlink) {
   if (!out) {
     set_error("out is NULL");
     return SSM_EINVAL;
@@ -771,6 +774,7 @@ ssm_status plan_create(ssm_plan_t* out, const ssm_params* p, const double* K_hos
   pl->p = *p;
   pl->device = device;
   pl->waves = std::max(1, waves);
+  pl->g.zlink = zlink ? 1 : 0;
   ssm_status st = plan_impl(pl, K_host, s);
   if (st != SSM_OK) {
     cudaStreamSynchronize(s);
@@ -817,6 +821,29 @@ ssm_status ssm_plan_ex(ssm_plan_t* out, const ssm_params* p, const double* K_hos
     return SSM_EINVAL;
   }
   return plan_create(out, p, K_host, device, static_cast<cudaStream_t>(stream), launch_waves);
+}
+
+ssm_status ssm_plan_batched(ssm_plan_t* out, const ssm_params* p, int64_t nbatch,
+                            const double* K_host, int device, void* stream, int launch_waves) {
+  if (!out || !p) {
+    set_error("NULL argument");
+    return SSM_EINVAL;
+  }
+  *out = nullptr;
+  if (p->ndim < 1 || p->ndim > 2) {
+    set_error("a batched plan stacks 1D or 2D slices (ndim 1 or 2)");
+    return SSM_EINVAL;
+  }
+  if (nbatch < 1 || nbatch > (int64_t)1 << 31 || launch_waves < 1 || launch_waves > 64) {
+    set_error("nbatch must be >= 1 and launch_waves in [1, 64]");
+    return SSM_EINVAL;
+  }
+  ssm_params q = *p;
+  if (q.ndim == 1) q.dims[1] = 1;
+  q.ndim = 3;
+  q.dims[2] = nbatch;
+  return plan_create(out, &q, K_host, device, static_cast<cudaStream_t>(stream), launch_waves,
+                     false);
 }
 
 ssm_status ssm_solve(ssm_plan_t plan, const float* M_dev, int64_t ldm, float* F_dev, int64_t ldf,

@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(UV) dense_update_kernel(UpdateArgs a) {
   const bool hxp = valid && x < nx - 1 && (!mk || mk[n + 1]);
   const bool hym = valid && y > 0 && (!mk || mk[n - sy_]);
   const bool hyp = valid && y < ny - 1 && (!mk || mk[n + sy_]);
-  const bool hzm = valid && zc > 0 && (!mk || mk[n - sz_]);
-  const bool hzp = valid && zc < nz - 1 && (!mk || mk[n + sz_]);
+  const bool hzm = a.g.zlink && valid && zc > 0 && (!mk || mk[n - sz_]);
+  const bool hzp = a.g.zlink && valid && zc < nz - 1 && (!mk || mk[n + sz_]);
   const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
   float s1 = 0.f, s2 = 0.f, s3 = 0.f;
   const int q0 = blockIdx.y * UQ, q1 = min(a.Q, q0 + UQ);
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(UV) objective_kernel(const float* __restrict__
         const float dd = v - row[n + sy];
         acc = fmaf(dd, dd, acc);
       }
-      if (z + 1 < g.nz && (!mk || mk[n + sz])) {
+      if (g.zlink && z + 1 < g.nz && (!mk || mk[n + sz])) {
         const float dd = v - row[n + sz];
         acc = fmaf(dd, dd, acc);
       }

@@ -62,6 +62,7 @@ struct Grid {
   int nx, ny, nz;     // nz = 1 for 2D, ny = nz = 1 for 1D
   int64_t N;          // nx*ny*nz
   int64_t ld;         // leading dimension of every map-major Q x N array (elements)
+  int zlink = 1;      // 0: the z axis stacks independent slices (no smoothness across it)
 };
 
 // the largest padded rank the fused low-rank kernel is instantiated for
@@ -170,7 +171,7 @@ ssm_status plan_footprint(const ssm_params& p, bool staging, int waves, int64_t*
                           int64_t* peak);
 // ssm_plan with the launch-waves setting
 ssm_status plan_create(ssm_plan_t* out, const ssm_params* p, const double* K_host, int device,
-                       cudaStream_t s, int waves);
+                       cudaStream_t s, int waves, bool zlink = true);
 
 // ------------------------------------------------------------------------------------
 // launchers (each returns a status; the stream is the caller's)

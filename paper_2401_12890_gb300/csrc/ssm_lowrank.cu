@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
   const int64_t N = a.g.N;
   const int Q = a.Q;
   const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const int NR = (ny > 1 ? 2 : 0) + (nz > 1 ? 2 : 0);
+  const bool zl = nz > 1 && a.g.zlink;   // z neighbours coupled
+  const int NR = (ny > 1 ? 2 : 0) + (zl ? 2 : 0);
   const Layout L(R, NR);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + NB;
@@ -208,8 +209,8 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
       const bool hxp = in && x < nx - 1 && (!mk || mk[n + 1]);
       const bool hym = in && y > 0 && (!mk || mk[n - nx]);
       const bool hyp = in && y < ny - 1 && (!mk || mk[n + nx]);
-      const bool hzm = in && zc > 0 && (!mk || mk[n - plane]);
-      const bool hzp = in && zc < nz - 1 && (!mk || mk[n + plane]);
+      const bool hzm = zl && in && zc > 0 && (!mk || mk[n - plane]);
+      const bool hzp = zl && in && zc < nz - 1 && (!mk || mk[n + plane]);
       const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
       const float e1 = (a.xi + a.beta - a.lam_s * deg) * a.inv_xb;   // weight of z
       int nidx[4];
@@ -342,7 +343,8 @@ size_t smem_for(int nr) { return (size_t)Layout(R, nr).total + 128; }
 template <int R>
 ssm_status launch_r(const LowrankMaps& maps, const LowrankArgs& args, bool check, int64_t grid,
                     cudaStream_t s) {
-  const size_t shm = smem_for<R>((args.g.ny > 1 ? 2 : 0) + (args.g.nz > 1 ? 2 : 0));
+  const size_t shm =
+      smem_for<R>((args.g.ny > 1 ? 2 : 0) + (args.g.nz > 1 && args.g.zlink ? 2 : 0));
   if (check)
     lowrank_iter_kernel<R, true><<<(unsigned)grid, NT, shm, s>>>(maps, args);
   else
@@ -405,7 +407,7 @@ int bpsm_for(int R, int nr) {
 
 // persistent grid: every resident slot, but at least two stages of rows per CTA
 int64_t lowrank_grid(const ssm_plan_s* pl) {
-  const int nr = (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 ? 2 : 0);
+  const int nr = (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 && pl->g.zlink ? 2 : 0);
   const int64_t ntiles = (pl->g.N + TV - 1) / TV;
   const int64_t T = ntiles * pl->Q;
   int64_t grid = (int64_t)sm_count() * bpsm_for(pl->R, nr) * std::max(1, pl->waves);

@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t ld = a.g.ld, N = a.g.N;
   const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const int NR = (ny > 1 ? 2 : 0) + (nz > 1 ? 2 : 0);
+  const bool zl = nz > 1 && a.g.zlink;   // z neighbours coupled
+  const int NR = (ny > 1 ? 2 : 0) + (zl ? 2 : 0);
   const ULayout L(NR);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + UNB;
@@ -154,8 +155,8 @@ __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
       const bool hxp = in && x < nx - 1 && (!mk || mk[n + 1]);
       const bool hym = in && y > 0 && (!mk || mk[n - nx]);
       const bool hyp = in && y < ny - 1 && (!mk || mk[n + nx]);
-      const bool hzm = in && zc > 0 && (!mk || mk[n - plane]);
-      const bool hzp = in && zc < nz - 1 && (!mk || mk[n + plane]);
+      const bool hzm = zl && in && zc > 0 && (!mk || mk[n - plane]);
+      const bool hzp = zl && in && zc < nz - 1 && (!mk || mk[n + plane]);
       const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
       const bool flags[4] = {ny > 1 ? hym : hzm, ny > 1 ? hyp : hzp, hzm, hzp};
       int nidx[4];
@@ -241,7 +242,9 @@ __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
   }
 }
 
-int update_nr(const ssm_plan_s* pl) { return (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 ? 2 : 0); }
+int update_nr(const ssm_plan_s* pl) {
+  return (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 && pl->g.zlink ? 2 : 0);
+}
 
 // consumer warps of the kernel for this grid
 int update_ncw(const ssm_plan_s* pl) { return update_nr(pl) == 4 ? 16 : 8; }

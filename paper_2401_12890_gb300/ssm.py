@@ -140,6 +140,8 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_plan_ex.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SsmParams), vp, ctypes.c_int, vp,
                                 ctypes.c_int]
+    lib.ssm_plan_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SsmParams), i64, vp,
+                                     ctypes.c_int, vp, ctypes.c_int]
     lib.ssm_server_submit_device.argtypes = [vp, ctypes.POINTER(SsmParams), vp, vp, i64, vp, i64,
                                              ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_plan_set_graphs.argtypes = [vp, ctypes.c_int]
@@ -170,7 +172,7 @@ def load_library(path: str = LIB_PATH):
                  "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
                  "ssm_plan_ex", "ssm_server_submit_device", "ssm_plan_set_beta",
                  "ssm_tune_beta", "ssm_plan_launch_info", "ssm_plan_set_mask",
-                 "ssm_selftest_wait_timeout",
+                 "ssm_selftest_wait_timeout", "ssm_plan_batched",
                  "ssm_plan_footprint", "ssm_plan_device_bytes", "ssm_server_default_config",
                  "ssm_server_create", "ssm_server_submit", "ssm_server_poll", "ssm_server_wait",
                  "ssm_server_stats_read", "ssm_server_destroy"):
@@ -251,7 +253,10 @@ class Plan:
 
     def __init__(self, K, dims, lam, beta, *, form="lowrank", precision="fp32", rank=0,
                  rank_tol=5e-5, xi_p=0.0, stencil_pairs=2, max_iter=300, check_every=10,
-                 tol_primal=0.0, tol_change=0.0, device=0, stream=None, launch_waves=1):
+                 tol_primal=0.0, tol_change=0.0, device=0, stream=None, launch_waves=1,
+                 batch=None):
+        """batch=B: B independent slices of the grid `dims` (1D or 2D) sharing K, solved
+        together (ssm_plan_batched); M and F then hold the slices one after another."""
         lib = load_library()
         K = np.ascontiguousarray(K, dtype=np.float64)
         p = make_params(K.shape[0], K.shape[1], dims, lam, beta, form=form,
@@ -262,12 +267,17 @@ class Plan:
         self.params = p
         self.dims = dims
         self.P, self.Q = p.P, p.Q
-        self.N = int(np.prod(dims))
+        self.N = int(np.prod(dims)) * (int(batch) if batch else 1)
         self.device = device
         self._h = ctypes.c_void_p()
-        st = lib.ssm_plan_ex(ctypes.byref(self._h), ctypes.byref(p),
-                             K.ctypes.data_as(ctypes.c_void_p), int(device),
-                             _stream_handle(stream), int(launch_waves))
+        if batch:
+            st = lib.ssm_plan_batched(ctypes.byref(self._h), ctypes.byref(p), int(batch),
+                                      K.ctypes.data_as(ctypes.c_void_p), int(device),
+                                      _stream_handle(stream), int(launch_waves))
+        else:
+            st = lib.ssm_plan_ex(ctypes.byref(self._h), ctypes.byref(p),
+                                 K.ctypes.data_as(ctypes.c_void_p), int(device),
+                                 _stream_handle(stream), int(launch_waves))
         if st != SSM_OK:
             raise SsmError(st, "ssm_plan")
 
