@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline form only")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
+    ap.add_argument("--no-batching", action="store_true", help="skip the batching run")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-iters", type=int, default=100,
                     help="iterations per served request (a fixed budget)")
@@ -362,6 +363,9 @@ def bench_ours(args):
     serving = None
     if dist.world == 1 and not args.no_serving:
         serving = bench_serving(args)
+    batching = None
+    if dist.world == 1 and not args.no_batching:
+        batching = bench_batching()
 
     if dist.rank == 0:
         hl = headline
@@ -384,6 +388,7 @@ def bench_ours(args):
             "forms": results,
             "err_vs_oracle": cpu and cpu["errors"],
             "serving": serving,
+            "batching": batching,
         }
         print(json.dumps(out), flush=True)
     dist.close()
@@ -532,6 +537,61 @@ def bench_serving(args):
         }
         torch.cuda.empty_cache()
     return out
+
+# --------------------------------------------------------------------------------------
+# batching: many small slices sharing a dictionary, one plan for all of them
+# --------------------------------------------------------------------------------------
+BATCH_SLICES = 64
+
+
+def bench_batching():
+    """64 slices of the 32 x 32 diffusion-relaxation workload (P = 30, Q = 225), 300
+    iterations each: 64 solves in turn on one plan, against one batched plan
+    (ssm_plan_batched) solving all slices in the same launches."""
+    import torch
+
+    from paper_2401_12890_gb300 import ssm, synth
+    w = synth.WORKLOADS["dr2d_tiny"]
+    K = synth.dictionary_for("dr2d_tiny")
+    Ms = [synth.make_problem("dr2d_tiny", seed=w.seed + 10 * b)[1] for b in range(BATCH_SLICES)]
+    Mall = torch.from_numpy(np.ascontiguousarray(np.concatenate(Ms, axis=1))).cuda()
+    Md = [torch.from_numpy(np.ascontiguousarray(m)).cuda() for m in Ms]
+    work = BATCH_SLICES * w.N * w.Q * w.iters
+    out = {"slices": BATCH_SLICES, "slice": f"{w.dims[0]}x{w.dims[1]}, P={w.P}, Q={w.Q}",
+           "iterations": w.iters, "unit": METRIC, "forms": {}}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for form, prec in (("lowrank", "fp32"), ("dense", "bf16x3")):
+        kw = dict(form=form, precision=prec, max_iter=w.iters, check_every=0)
+        one = ssm.Plan(K, w.dims, w.lam, w.beta, **kw)
+        one.set_graphs(True)
+        F1 = torch.empty((w.Q, w.N), dtype=torch.float32, device="cuda")
+        for m in Md[:2]:
+            one.solve_async(m, F1)
+        torch.cuda.synchronize()
+        e0.record()
+        for m in Md:
+            one.solve_async(m, F1)
+        e1.record()
+        torch.cuda.synchronize()
+        t_seq = e0.elapsed_time(e1) / 1e3
+        one.close()
+        bat = ssm.Plan(K, w.dims, w.lam, w.beta, batch=BATCH_SLICES, **kw)
+        bat.set_graphs(True)
+        FB = torch.empty((w.Q, w.N * BATCH_SLICES), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            bat.solve_async(Mall, FB)
+        torch.cuda.synchronize()
+        e0.record()
+        bat.solve_async(Mall, FB)
+        e1.record()
+        torch.cuda.synchronize()
+        t_bat = e0.elapsed_time(e1) / 1e3
+        bat.close()
+        out["forms"][form_key(form, prec)] = {
+            "one_by_one_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
+            "one_by_one_value": work / t_seq, "batched_value": work / t_bat}
+    return out
+
 
 # --------------------------------------------------------------------------------------
 # reference arm: the FP64 oracle itself on the host cores
