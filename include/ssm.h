@@ -299,9 +299,13 @@ typedef struct {
   int gemm_tile_n;         /* tensor-core GEMM compartment-tile width (autotuned), 0
                               when the plan has no tensor-core product              */
   int gemm_grid;           /* CTAs of the tensor-core GEMM                           */
-  int update_grid;         /* CTAs of the tensor-core form's update kernel           */
+  int update_grid;         /* CTAs of the tensor-core form's update kernel (two-kernel
+                              iteration only)                                       */
   int lowrank_grid;        /* CTAs of the fused low-rank kernel                      */
   int sm_count;            /* SMs of the plan's device                               */
+  int tc_fused;            /* 1: the tensor-core iteration is one kernel (the update
+                              in the GEMM's epilogue); 0: GEMM + update kernel. Chosen
+                              at plan time by timing both; results are identical    */
 } ssm_launch_info;
 
 ssm_status ssm_plan_launch_info(ssm_plan_t plan, ssm_launch_info* out);

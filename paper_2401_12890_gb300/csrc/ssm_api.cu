@@ -323,6 +323,10 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   if (st != SSM_OK) return st;
   if (p.form != SSM_FORM_LOWRANK) SSM_TRY(form_dense_inverse(pl, s));
 
+  // the device error word first: the tuning launches below report into it
+  SSM_TRY(palloc(pl, &pl->dev_err, 1, s));
+  SSM_CUDA(cudaMemsetAsync(pl->dev_err, 0, sizeof(int), s));
+
   // per-voxel state
   const size_t QN = (size_t)Q * pl->g.ld;
   if (p.form != SSM_FORM_ADMM)
@@ -377,8 +381,6 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   pl->red_cap = maxparts;
   SSM_TRY(palloc(pl, &pl->red, (size_t)maxparts * 4, s));
   SSM_TRY(palloc(pl, &pl->red_out, 8, s));
-  SSM_TRY(palloc(pl, &pl->dev_err, 1, s));
-  SSM_CUDA(cudaMemsetAsync(pl->dev_err, 0, sizeof(int), s));
   SSM_CUDA(cudaMallocHost(&pl->red_host, 8 * sizeof(double)));
   SSM_CUDA(cudaEventRecord(pl->ev1, s));
   SSM_CUDA(cudaEventSynchronize(pl->ev1));
@@ -561,7 +563,12 @@ ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, bool check_next, i
     SSM_TRY(prof_mark(pl, false, s));
     return dense_update(pl, cur, pl->Acc, check, true, false, pl->red, nparts, s);
   }
-  // the dominant kernel of the tensor-core form is the product M w
+  if (pl->tc_fused) {
+    // one kernel: the product M w with the element-wise steps in its epilogue
+    SSM_TRY(tc_iteration(pl, cur, check, pl->red, nparts, s));
+    return prof_mark(pl, false, s);
+  }
+  // two kernels; the dominant one is the product M w
   SSM_TRY(tc_gemm(pl, cur, s));
   SSM_TRY(prof_mark(pl, false, s));
   return tc_update(pl, cur, check, pl->red, nparts, s);
@@ -1034,6 +1041,7 @@ ssm_status ssm_plan_launch_info(ssm_plan_t plan, ssm_launch_info* out) {
     out->gemm_tile_n = plan->tc_bn;
     out->gemm_grid = tc_gemm_grid(plan);
     out->update_grid = tc_update_grid(plan);
+    out->tc_fused = plan->tc_fused ? 1 : 0;
   }
   return SSM_OK;
 }

@@ -65,6 +65,25 @@ struct Grid {
   int zlink = 1;      // 0: the z axis stacks independent slices (no smoothness across it)
 };
 
+// One element of the full-rank iteration's z-step (Eq. 31, with D^T D z = s (deg z -
+// sum_nbr z)) and dual step (step 11), given f = h + M w:
+//     z' = max(0, (xi z - lambda s (deg z - nb) + beta f + d) / (xi + beta))
+//     d' = d - beta (z' - f),   w' = beta z' - d'
+// Every rounding is explicit (fmaf / __fmul_rn), so each kernel that applies the step
+// produces the same bits whatever the compiler would otherwise contract.
+struct DenseStep {
+  float xi, lam_s, beta, inv_xb;   // inv_xb = 1 / (xi + beta)
+  __device__ __forceinline__ float apply(float z, float d, float f, float deg, float nb, float& dn,
+                                         float& w) const {
+    const float lap = fmaf(deg, z, -nb);                                  // deg z - nb
+    const float num = fmaf(xi, z, fmaf(-lam_s, lap, fmaf(beta, f, d)));
+    const float zn = fmaxf(0.f, __fmul_rn(num, inv_xb));
+    dn = fmaf(-beta, __fsub_rn(zn, f), d);
+    w = fmaf(beta, zn, -dn);
+    return zn;
+  }
+};
+
 // the largest padded rank the fused low-rank kernel is instantiated for
 constexpr int kMaxRank = 64;
 
@@ -152,6 +171,7 @@ struct ssm_plan_s {
   int waves = 1;
   // compartment-tile width of the tensor-core GEMM (chosen by its autotuner)
   int tc_bn = 256;
+  bool tc_fused = true;         // tensor-core form: one fused GEMM + update kernel per iteration
   // Algorithm 1 (SSM_FORM_ADMM): state, per-axis DCT matrices (forward, inverse), scaling
   ssm::AdmmState adm{};
   float* adm_T[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};

@@ -1,14 +1,19 @@
 // Full-rank (Eq. 26) LADMM iteration on the tcgen05 tensor cores, BF16 split products.
 //
 // The f-step of Eq. 26 is f = h + M w with M = (K^T K + beta I)^{-1} (Q x Q, formed
-// once in FP64), h = M g (once per solve) and w = beta z - d. An iteration is two
-// kernels:
-//   tc_gemm_kernel    acc = M w on the tensor cores (tcgen05.mma, TMA-fed, FP32 in TMEM)
-//   tc_update_kernel  the bandwidth-bound rest, TMA-staged (ssm_tc_update.cu):
+// once in FP64), h = M g (once per solve) and w = beta z - d. The iteration is
+//   acc = M w on the tensor cores (tcgen05.mma, TMA-fed, FP32 in TMEM), then per element
 //       f  = h + acc
 //       z' = max(0, (xi z - lambda s (deg z - sum_nbr z) + beta f + d) / (xi + beta))  (Eq. 31)
 //       d' = d - beta (z' - f)                                                      (step 11)
 //       w' = beta z' - d'   -> stored as the BF16 pair (hi, lo) for the next product
+// One kernel does all of it: the epilogue warps apply the element-wise steps to each
+// accumulator tile straight out of TMEM while the MMA warp computes the next tile, so
+// the update's HBM traffic runs under the tensor-core time and M w never goes to
+// memory. (The same GEMM with a plain store epilogue, acc -> memory, followed by the
+// separate TMA-staged update kernel of ssm_tc_update.cu, is kept as the two-kernel
+// form: the tile-width autotuner times that GEMM, and it is the reference the fused
+// kernel is tested against bit for bit.)
 //
 // Precision ("BF16x3"): w and M are each split into BF16 hi + lo parts
 // (x_hi = bf16(x), x_lo = bf16(x - x_hi)), and M w is accumulated in FP32 in tensor
@@ -37,13 +42,18 @@
 #include "ssm_internal.cuh"
 #include "ssm_tma.cuh"
 
+#ifndef SSM_TC_NEPI
+#define SSM_TC_NEPI 8
+#endif
+
 namespace ssm {
 namespace {
 
 constexpr int BM = 128;                         // voxels per tile (MMA M, TMEM lanes)
 constexpr int BK = 64;                          // K per stage: one 128-byte swizzle atom
 constexpr int UK = 16;                          // K per tcgen05.mma (kind::f16)
-constexpr int NTHR = 192;                       // TMA warp, MMA warp, 4 epilogue warps
+constexpr int NEPI = SSM_TC_NEPI;                // epilogue warps (2 per TMEM lane quarter)
+constexpr int NTHR = 64 + 32 * NEPI;            // TMA warp, MMA warp, epilogue warps
 constexpr uint32_t TMEM_COLS = 512;             // two accumulators, at columns 0 and 256
 constexpr int A_BYTES = BM * BK * 2;            // 16 KB
 constexpr int kSmemLimit = 227 * 1024;
@@ -74,11 +84,36 @@ struct TcMaps {
 };
 
 struct TcArgs {
-  float* __restrict__ Acc;           // M w, map-major Q x N (row stride ld)
+  float* __restrict__ Acc;           // M w, map-major Q x N (row stride ld): store epilogue
   int* __restrict__ err;
   Grid g;
   int Q, ntv, ntq;
+  // fused update epilogue
+  const float* __restrict__ Zin;     // z^k, d^k, h (Q x ld)
+  const float* __restrict__ Din;
+  const float* __restrict__ H;
+  float* __restrict__ Zout;          // z^{k+1}, d^{k+1}
+  float* __restrict__ Dout;
+  __nv_bfloat16* __restrict__ Whi;   // w^{k+1} split, voxel-major (row stride Qp)
+  __nv_bfloat16* __restrict__ Wlo;
+  double* __restrict__ partial;      // 4 doubles per CTA (residual iterations)
+  const uint8_t* __restrict__ mask;  // voxels inside the object (nullptr: every voxel)
+  int Qp;
+  float beta, xi, lam_s, inv_xb;
 };
+
+// compartments per load group of the fused epilogue (reads in flight per thread)
+constexpr int UG = 8;   // one tcgen05.ld of 8 columns and one 16-byte store of w each
+
+// epilogue modes of tc_gemm_kernel
+constexpr int EPI_STORE = 0;         // acc -> Acc
+constexpr int EPI_UPDATE = 1;        // the element-wise steps of the iteration
+constexpr int EPI_UPDATE_CHECK = 2;  // ... plus the residual sums of the stopping rule
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
+  return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
+}
 
 // shared-memory matrix descriptor, K-major operand in the 128-byte swizzle layout:
 // start address >> 4 (bits 0-13), leading byte offset 16 B (unused for this layout),
@@ -130,7 +165,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int BN>
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN, int EPI>
 __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant__ TcMaps maps,
                                                           const TcArgs a) {
   constexpr int NS = Tile<BN>::NS, STAGE_BYTES = Tile<BN>::STAGE_BYTES;
@@ -153,7 +201,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 4);
+      mbar_init(&tempty[i], NEPI);
     }
     mbar_fence_init();
   }
@@ -172,6 +220,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
   const int ntiles = a.ntv * a.ntq;
   const int nk = (a.Q + BK - 1) / BK;
   bool failed = false;
+  float s1 = 0.f, s2 = 0.f, s3 = 0.f;   // residual sums of the fused update
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -235,7 +284,16 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
     // ------------------------------------------------------------ accumulator drain
     const int quarter = warp & 3;                  // TMEM lanes 32*quarter .. +31
     const int row = quarter * 32 + lane;           // voxel within the tile
+    const int half = NEPI == 8 ? (warp - 2) >> 2 : 0;   // which column groups this warp takes
     const int64_t ld = a.g.ld, N = a.g.N;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const bool zl = nz > 1 && a.g.zlink;           // z neighbours coupled
+    const int NR = (ny > 1 ? 2 : 0) + (zl ? 2 : 0);
+    const int64_t plane = (int64_t)nx * ny;
+    // neighbour offsets beyond x: -nx, +nx, -nx*ny, +nx*ny (the axes the grid has; the y
+    // pair first when there is a y axis)
+    const int64_t off[4] = {ny > 1 ? -(int64_t)nx : -plane, ny > 1 ? (int64_t)nx : plane,
+                            -plane, plane};
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       const int acc = it & 1, ra = it >> 1;
@@ -244,7 +302,101 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
       const int vt = t / a.ntq, qt = t % a.ntq;
       const int64_t n = (int64_t)vt * BM + row;
       const bool valid = n < N && !failed;
-      for (int cc = 0; cc < BN / 32; ++cc) {
+      if constexpr (EPI != EPI_STORE) {
+        // the voxel's neighbours on the grid graph (the one the mask induces: a voxel
+        // outside the object is left alone and is nobody's neighbour)
+        int x = 0, y = 0, zc = 0;
+        if (valid) {
+          x = (int)(n % nx);
+          const int64_t tt = n / nx;
+          y = (int)(tt % ny);
+          zc = (int)(tt / ny);
+        }
+        const uint8_t* mk = a.mask;
+        const bool in = valid && (!mk || mk[n]);
+        const bool hxm = in && x > 0 && (!mk || mk[n - 1]);
+        const bool hxp = in && x < nx - 1 && (!mk || mk[n + 1]);
+        const bool hym = in && y > 0 && (!mk || mk[n - nx]);
+        const bool hyp = in && y < ny - 1 && (!mk || mk[n + nx]);
+        const bool hzm = zl && in && zc > 0 && (!mk || mk[n - plane]);
+        const bool hzp = zl && in && zc < nz - 1 && (!mk || mk[n + plane]);
+        const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
+        const bool flags[4] = {ny > 1 ? hym : hzm, ny > 1 ? hyp : hzp, hzm, hzp};
+        bool nok[4];
+        int64_t dk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          nok[j] = j < NR && flags[j];
+          dk[j] = nok[j] ? off[j] : 0;
+        }
+        const int dxm = hxm ? -1 : 0, dxp = hxp ? 1 : 0;
+        // groups of UG compartments of voxel n: a group's loads (coalesced across the
+        // warp's 32 voxels; the neighbours are L1/L2 hits) are issued before its stores
+        const DenseStep step{a.xi, a.lam_s, a.beta, a.inv_xb};
+#pragma unroll 1
+        for (int cg = half; cg < BN / UG; cg += NEPI / 4) {
+          const int q0 = qt * BN + cg * UG;
+          if (q0 >= a.Q) break;                     // uniform across the warp
+          float v[UG];
+          tmem_ld8(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 256 + cg * UG),
+                   v);
+          if (in) {
+            // every load of the group is issued before any arithmetic: absent neighbours
+            // read the voxel's own value (a valid address) and are dropped by selects
+            float zz[UG], dd[UG], hv[UG], nbv[UG];
+#pragma unroll
+            for (int j = 0; j < UG; ++j) {
+              // a padding column reads the last compartment's row (in bounds), unused
+              const int64_t o = (int64_t)min(q0 + j, a.Q - 1) * ld + n;
+              zz[j] = __ldg(a.Zin + o);
+              dd[j] = __ldg(a.Din + o);
+              hv[j] = __ldg(a.H + o);
+              const float zxm = __ldg(a.Zin + o + dxm), zxp = __ldg(a.Zin + o + dxp);
+              float zk[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) zk[k] = k < NR ? __ldg(a.Zin + o + dk[k]) : 0.f;
+              float nb = 0.f;
+              nb += hxm ? zxm : 0.f;
+              nb += hxp ? zxp : 0.f;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) nb += nok[k] ? zk[k] : 0.f;
+              nbv[j] = nb;
+            }
+            uint32_t hh[UG / 2], ll[UG / 2];
+#pragma unroll
+            for (int j = 0; j < UG; ++j) {
+              const int q = q0 + j;
+              float w = 0.f;                        // padding columns stay zero
+              if (q < a.Q) {
+                const int64_t o = (int64_t)q * ld + n;
+                const float f = __fadd_rn(hv[j], v[j]);
+                float dn;
+                const float zn = step.apply(zz[j], dd[j], f, deg, nbv[j], dn, w);
+                a.Zout[o] = zn;
+                a.Dout[o] = dn;
+                if constexpr (EPI == EPI_UPDATE_CHECK) {
+                  const float e = zn - f, ch = zn - zz[j];
+                  s1 = fmaf(e, e, s1);
+                  s2 = fmaf(ch, ch, s2);
+                  s3 = fmaf(zn, zn, s3);
+                }
+              }
+              v[j] = w;
+            }
+#pragma unroll
+            for (int e = 0; e < UG / 2; ++e) {
+              const float w0 = v[2 * e], w1 = v[2 * e + 1];
+              hh[e] = pack_bf16x2(w0, w1);
+              ll[e] = pack_bf16x2(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
+                                  w1 - __bfloat162float(__float2bfloat16_rn(w1)));
+            }
+            *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+            *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+          }
+          __syncwarp();
+        }
+      } else
+      for (int cc = half; cc < BN / 32; cc += NEPI / 4) {
         const int q0 = qt * BN + cc * 32;
         if (q0 >= a.Q) break;                       // uniform across the warp
         float v[32];
@@ -263,6 +415,26 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
     }
   }
   if (failed) atomicExch(a.err, (int)SSM_ETIMEOUT);
+  if constexpr (EPI == EPI_UPDATE_CHECK) {
+    double d1 = s1, d2 = s2, d3 = s3;
+    for (int o = 16; o > 0; o >>= 1) {
+      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      d3 += __shfl_xor_sync(0xffffffffu, d3, o);
+    }
+    __shared__ double red[NTHR / 32][3];
+    if (lane == 0) {
+      red[warp][0] = d1;
+      red[warp][1] = d2;
+      red[warp][2] = d3;
+    }
+    __syncthreads();
+    if (tid < 3) {
+      double t = 0.0;
+      for (int w = 0; w < NTHR / 32; ++w) t += red[w][tid];
+      a.partial[(int64_t)blockIdx.x * 4 + tid] = t;
+    }
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -279,8 +451,8 @@ int gemm_grid(const ssm_plan_s* pl, int bn) {
   return std::max(1, std::min(sm_count() * std::max(1, pl->waves), ntv * ntq));
 }
 
-template <int BN>
-ssm_status launch_gemm(const ssm_plan_s* pl, int cur, cudaStream_t s) {
+template <int BN, int EPI>
+ssm_status launch_gemm(const ssm_plan_s* pl, int cur, double* partial, cudaStream_t s) {
   const uint64_t Q = (uint64_t)pl->Q, N = (uint64_t)pl->g.N, Qp = (uint64_t)pl->Qp;
   TcMaps m;
   const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
@@ -296,88 +468,150 @@ ssm_status launch_gemm(const ssm_plan_s* pl, int cur, cudaStream_t s) {
   a.Q = pl->Q;
   a.ntv = (int)((pl->g.N + BM - 1) / BM);
   a.ntq = (pl->Q + BN - 1) / BN;
-  tc_gemm_kernel<BN><<<gemm_grid(pl, BN), NTHR, Tile<BN>::SMEM_BYTES, s>>>(m, a);
+  a.Zin = pl->Z[cur];
+  a.Din = pl->Dl[cur];
+  a.H = pl->H;
+  a.Zout = pl->Z[cur ^ 1];
+  a.Dout = pl->Dl[cur ^ 1];
+  a.Whi = pl->Whi[cur ^ 1];
+  a.Wlo = pl->Wlo[cur ^ 1];
+  a.partial = partial;
+  a.mask = pl->mask;
+  a.Qp = pl->Qp;
+  a.beta = (float)pl->p.beta;
+  a.xi = (float)pl->xi;
+  a.lam_s = (float)pl->lam_s;
+  a.inv_xb = (float)(1.0 / (pl->xi + pl->p.beta));
+  tc_gemm_kernel<BN, EPI><<<gemm_grid(pl, BN), NTHR, Tile<BN>::SMEM_BYTES, s>>>(m, a);
   SSM_LAUNCHED();
   return SSM_OK;
 }
 
-ssm_status gemm_dispatch(const ssm_plan_s* pl, int bn, int cur, cudaStream_t s) {
+template <int EPI>
+ssm_status gemm_dispatch(const ssm_plan_s* pl, int bn, int cur, double* partial, cudaStream_t s) {
   switch (bn) {
-    case 256: return launch_gemm<256>(pl, cur, s);
-    case 224: return launch_gemm<224>(pl, cur, s);
-    case 192: return launch_gemm<192>(pl, cur, s);
-    case 160: return launch_gemm<160>(pl, cur, s);
-    case 128: return launch_gemm<128>(pl, cur, s);
+    case 256: return launch_gemm<256, EPI>(pl, cur, partial, s);
+    case 224: return launch_gemm<224, EPI>(pl, cur, partial, s);
+    case 192: return launch_gemm<192, EPI>(pl, cur, partial, s);
+    case 160: return launch_gemm<160, EPI>(pl, cur, partial, s);
+    case 128: return launch_gemm<128, EPI>(pl, cur, partial, s);
     default:
       set_error("tensor-core GEMM: unsupported tile width");
       return SSM_EUNSUPPORTED;
   }
 }
 
-template <int BN>
-cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Tile<BN>::SMEM_BYTES);
+ssm_status gemm_dispatch(const ssm_plan_s* pl, int bn, int cur, cudaStream_t s) {
+  return gemm_dispatch<EPI_STORE>(pl, bn, cur, nullptr, s);
 }
 
-// tile widths measured per (device, Q, N, waves), shared by every plan of the process
-std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int64_t, int>, int> g_tuned;
+template <int BN>
+cudaError_t set_smem_attr() {
+  for (const void* k : {(const void*)tc_gemm_kernel<BN, EPI_STORE>,
+                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE>,
+                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE_CHECK>}) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
-// Autotuner: time every tile width on the plan's own operands (one warm-up launch, then
-// two timed launches each, CUDA events on the plan's stream) and keep the fastest.
-// The choice does not change results: each output element sums the same products in
-// the same K order whatever the tile width.
+// choices measured per (device, Q, N, waves, halo rows, fixed tile width), shared by every
+// plan of the process
+struct TcChoice {
+  int bn;
+  bool fused;
+};
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int64_t, int, int, int>, TcChoice> g_tuned;
+
+// Autotuner, on the plan's own operands and state buffers (the solve initialises the
+// state, so what these launches write is overwritten): (1) the tile width, timing the
+// GEMM alone at every width that pads Q to fewer columns than a wider one; (2) at that
+// width, the fused iteration kernel against the GEMM + update pair -- the fused kernel
+// wins where its epilogue hides under the tensor-core time (large Q) and loses where the
+// element-wise work outweighs the product (small Q). Each candidate gets one warm-up
+// launch and two timed ones (CUDA events on the plan's stream). Neither choice changes
+// results: each output element sums the same products in the same K order whatever the
+// width, and both iteration forms apply the same steps to the same accumulator values.
+// SSM_TC_BN / SSM_TC_FUSED fix a choice (tests and sweeps).
 ssm_status tune_tile(ssm_plan_s* pl, cudaStream_t s) {
-  if (const char* env = getenv("SSM_TC_BN")) {   // a fixed width (tests and sweeps)
+  int fixed_bn = 0, fixed_fused = -1;
+  if (const char* env = getenv("SSM_TC_BN")) {
     const int v = atoi(env);
     for (int bn : kTileN)
-      if (bn == v) {
-        pl->tc_bn = v;
-        return SSM_OK;
-      }
+      if (bn == v) fixed_bn = v;
   }
-  const auto key = std::make_tuple(pl->device, pl->Q, pl->g.N, pl->waves);
+  if (const char* env = getenv("SSM_TC_FUSED")) fixed_fused = atoi(env) != 0 ? 1 : 0;
+  if (fixed_bn != 0 && fixed_fused >= 0) {
+    pl->tc_bn = fixed_bn;
+    pl->tc_fused = fixed_fused != 0;
+    return SSM_OK;
+  }
+  const int nr = (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 && pl->g.zlink ? 2 : 0);
+  const auto key = std::make_tuple(pl->device, pl->Q, pl->g.N, pl->waves, nr, fixed_bn);
+  auto apply = [&](const TcChoice& c) {
+    pl->tc_bn = c.bn;
+    pl->tc_fused = fixed_fused >= 0 ? fixed_fused != 0 : c.fused;
+  };
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      pl->tc_bn = it->second;
+      apply(it->second);
       return SSM_OK;
     }
   }
   cudaEvent_t e0, e1;
   SSM_CUDA(cudaEventCreate(&e0));
   SSM_CUDA(cudaEventCreate(&e1));
-  int best = 256;
-  float best_ms = 0.f;
+  // one warm-up launch of `run`, then the time of two
+  auto timed = [&](auto&& run, float* ms) -> ssm_status {
+    SSM_TRY(run());
+    SSM_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 2; ++r) SSM_TRY(run());
+    SSM_CUDA(cudaEventRecord(e1, s));
+    SSM_CUDA(cudaEventSynchronize(e1));
+    SSM_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return SSM_OK;
+  };
+  TcChoice c{fixed_bn != 0 ? fixed_bn : 256, false};
   ssm_status st = SSM_OK;
-  for (int bn : kTileN) {
-    // a width whose tiles do not cover fewer padded columns than a wider one cannot win
-    const int pad = (pl->Q + bn - 1) / bn * bn;
-    if (bn != 256 && pad >= (pl->Q + 255) / 256 * 256) continue;
-    st = gemm_dispatch(pl, bn, 0, s);
-    if (st != SSM_OK) break;
-    if (cudaEventRecord(e0, s) != cudaSuccess) { st = SSM_ECUDA; break; }
-    for (int r = 0; r < 2 && st == SSM_OK; ++r) st = gemm_dispatch(pl, bn, 0, s);
-    if (st != SSM_OK) break;
-    float ms = 0.f;
-    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-      st = SSM_ECUDA;
-      break;
+  if (fixed_bn == 0) {
+    float best_ms = 0.f;
+    for (int bn : kTileN) {
+      // a width whose tiles do not cover fewer padded columns than a wider one cannot win
+      const int pad = (pl->Q + bn - 1) / bn * bn;
+      if (bn != 256 && pad >= (pl->Q + 255) / 256 * 256) continue;
+      float ms = 0.f;
+      st = timed([&] { return gemm_dispatch(pl, bn, 0, s); }, &ms);
+      if (st != SSM_OK) break;
+      if (bn == 256 || ms < best_ms) {
+        c.bn = bn;
+        best_ms = ms;
+      }
     }
-    if (bn == 256 || ms < best_ms) {
-      best = bn;
-      best_ms = ms;
-    }
+  }
+  if (st == SSM_OK) {
+    float two_ms = 0.f, fused_ms = 0.f;
+    int parts = 0;
+    st = timed(
+        [&] {
+          SSM_TRY(gemm_dispatch(pl, c.bn, 0, s));
+          return tc_update(pl, 0, false, nullptr, &parts, s);
+        },
+        &two_ms);
+    if (st == SSM_OK)
+      st = timed([&] { return gemm_dispatch<EPI_UPDATE>(pl, c.bn, 0, nullptr, s); }, &fused_ms);
+    c.fused = fused_ms < two_ms;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SSM_OK) return st;
-  pl->tc_bn = best;
+  apply(c);
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tuned[key] = best;
+  g_tuned[key] = c;
   return SSM_OK;
 }
 
@@ -412,8 +646,13 @@ int tc_gemm_grid(const ssm_plan_s* pl) { return gemm_grid(pl, pl->tc_bn); }
 
 ssm_status tc_iteration(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
                         cudaStream_t s) {
-  SSM_TRY(tc_gemm(pl, cur, s));
-  return tc_update(pl, cur, check, partial, nparts, s);
+  if (!pl->tc_fused) {
+    SSM_TRY(tc_gemm(pl, cur, s));
+    return tc_update(pl, cur, check, partial, nparts, s);
+  }
+  *nparts = gemm_grid(pl, pl->tc_bn);
+  return check ? gemm_dispatch<EPI_UPDATE_CHECK>(pl, pl->tc_bn, cur, partial, s)
+               : gemm_dispatch<EPI_UPDATE>(pl, pl->tc_bn, cur, partial, s);
 }
 
 }  // namespace ssm

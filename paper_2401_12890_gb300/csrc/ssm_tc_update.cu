@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
       const float* dr = reinterpret_cast<const float*>(st + L.dd);
       const float* hr = reinterpret_cast<const float*>(st + L.hh);
       const float* ar = reinterpret_cast<const float*>(st + L.aa);
+      const DenseStep step{a.xi, a.lam_s, a.beta, a.inv_xb};
       float wv[UQH];
 #pragma unroll
       for (int rr = 0; rr < UQH; ++rr) {
@@ -181,13 +182,12 @@ __global__ void __launch_bounds__(UWarps<UNCW>::NT) tc_update_kernel(
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             if (j < NR && flags[j]) nb += znr[(j * UQC + r) * UNW + nidx[j]];
-          const float f = hr[r * UTV + v] + ar[r * UTV + v];
-          const float zn = fmaxf(0.f, (a.xi * z - a.lam_s * (deg * z - nb) + a.beta * f + d) * a.inv_xb);
-          const float dn = d - a.beta * (zn - f);
+          const float f = __fadd_rn(hr[r * UTV + v], ar[r * UTV + v]);
+          float dn;
+          const float zn = step.apply(z, d, f, deg, nb, dn, wv[rr]);
           const int64_t o = (int64_t)q * ld + n;
           a.Zout[o] = zn;
           a.Dout[o] = dn;
-          wv[rr] = a.beta * zn - dn;
           if (CHECK) {
             const float e = zn - f, ch = zn - z;
             s1 = fmaf(e, e, s1);

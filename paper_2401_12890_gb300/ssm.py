@@ -91,6 +91,7 @@ class SsmLaunchInfo(ctypes.Structure):
     _fields_ = [
         ("launch_waves", ctypes.c_int), ("gemm_tile_n", ctypes.c_int), ("gemm_grid", ctypes.c_int),
         ("update_grid", ctypes.c_int), ("lowrank_grid", ctypes.c_int), ("sm_count", ctypes.c_int),
+        ("tc_fused", ctypes.c_int),
     ]
 
     def as_dict(self):

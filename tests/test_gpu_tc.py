@@ -123,3 +123,68 @@ def test_gemm_tile_widths_agree(monkeypatch, P, Q, dims, iters):
             assert rel(F, oracle["z"]) <= 1e-3
         else:
             assert np.array_equal(F, ref), f"tile width {bn} differs from 256"
+
+
+# ---------------------------------------------------------------------------
+# The fused iteration kernel (element-wise steps in the GEMM's epilogue) against the
+# two-kernel form (GEMM to memory, then the TMA-staged update kernel): the same FP32
+# steps with explicit roundings on the same accumulator values, so the iterates agree
+# bit for bit and the stopping decisions match -- on 1D, 2D, 3D and batched grids, with
+# a mask, at every tile width and with residual tests every few iterations. (The
+# residual norms sum the same terms in another order, so they agree to rounding.)
+# ---------------------------------------------------------------------------
+def solve_form(monkeypatch, fused, K, M, dims, lam, beta, iters, check_every, mask=None,
+               batch=None, bn=None):
+    monkeypatch.setenv("SSM_TC_FUSED", "1" if fused else "0")
+    if bn is not None:
+        monkeypatch.setenv("SSM_TC_BN", str(bn))
+    kw = {} if batch is None else {"batch": batch}
+    plan = ssm.Plan(K, dims, lam, beta, form="dense", precision="bf16x3", max_iter=iters,
+                    check_every=check_every, tol_primal=1e-4, tol_change=1e-4, **kw)
+    if mask is not None:
+        plan.set_mask(mask)
+    Md = torch.from_numpy(np.ascontiguousarray(M, np.float32)).cuda()
+    F, info = plan.solve(Md)
+    out = F.cpu().numpy()
+    plan.close()
+    return out, info
+
+
+FUSED_CASES = [
+    (30, 225, (32, 32), None),
+    (12, 300, (9, 9, 5), None),
+    (16, 70, (500,), None),
+    (24, 130, (37, 29), "mask"),
+    (20, 96, (16, 16, 6), "batch"),
+]
+
+
+@pytest.mark.parametrize("P,Q,dims,extra", FUSED_CASES,
+                         ids=["2d", "3d", "1d", "2d_mask", "batched_slices"])
+def test_fused_iteration_matches_two_kernel_form(monkeypatch, P, Q, dims, extra):
+    K, M, _ = synth.random_problem(P, Q, dims, seed=P + Q, snr=50.0)
+    kw = {}
+    if extra == "mask":
+        rng = np.random.default_rng(3)
+        kw["mask"] = rng.random(int(np.prod(dims))) > 0.2
+    if extra == "batch":   # slices of dims[:2] stacked along the last axis
+        kw["batch"] = dims[2]
+        dims = dims[:2]
+    F0, i0 = solve_form(monkeypatch, False, K, M, dims, 0.02, 1.5, 400, 7, **kw)
+    F1, i1 = solve_form(monkeypatch, True, K, M, dims, 0.02, 1.5, 400, 7, **kw)
+    assert i0["iterations"] == i1["iterations"]
+    # the residual norms sum the same values in another order (other work split)
+    assert i1["res_primal"] == pytest.approx(i0["res_primal"], rel=1e-6)
+    assert i1["res_change"] == pytest.approx(i0["res_change"], rel=1e-6)
+    assert np.array_equal(F0, F1)
+    if extra == "mask":
+        assert np.all(F1[:, ~kw["mask"]] == 0.0)
+
+
+@pytest.mark.parametrize("bn", [256, 224, 192, 160, 128])
+def test_fused_iteration_every_tile_width(monkeypatch, bn):
+    K, M, _ = synth.random_problem(64, 1600, (40, 30), seed=5, snr=50.0)
+    F0, i0 = solve_form(monkeypatch, False, K, M, (40, 30), 0.02, 1.5, 12, 4, bn=bn)
+    F1, i1 = solve_form(monkeypatch, True, K, M, (40, 30), 0.02, 1.5, 12, 4, bn=bn)
+    assert np.array_equal(F0, F1)
+    assert i1["res_primal"] == pytest.approx(i0["res_primal"], rel=1e-6)
