@@ -184,18 +184,24 @@ def form_key(form, prec):
     return f"{form}_{prec}"
 
 
-def dominant_kernel(form, prec, Q, N, r):
-    """(kernel name, source file, bound, algorithmic amount per launch, unit)."""
+def dominant_kernel(form, prec, Q, N, r, fused=False):
+    """(kernel name, source file, bound, algorithmic amount per launch, unit, traffic key).
+
+    The tensor-core form runs either the fused kernel (the GEMM with the update in its
+    epilogue: the whole iteration) or the GEMM + update pair, whichever the plan's
+    autotuner measured faster; its dominant kernel is the GEMM either way, and its bound
+    the tensor-core product's flops."""
     if form == "lowrank":
         # read z and write z' per state element (d cancels from the iteration, see
         # ssm_lowrank.cu); read S, u and write u' per voxel
         return ("lowrank_iter_kernel", "ssm_lowrank.cu", "hbm",
-                8.0 * Q * N + 12.0 * r * N, "GB/s")
+                8.0 * Q * N + 12.0 * r * N, "GB/s", "lowrank_iter_kernel")
     if prec == "fp32":
         # (for Algorithm 1 the profiled time is the whole iteration, of which the x-step
         # product is this amount of work)
-        return ("sgemm_kernel", "ssm_dense.cu", "alu", 2.0 * Q * Q * N, "TFLOP/s")
-    return ("tc_gemm_kernel", "ssm_tc.cu", "tensor", 3 * 2.0 * Q * Q * N, "TFLOP/s")
+        return ("sgemm_kernel", "ssm_dense.cu", "alu", 2.0 * Q * Q * N, "TFLOP/s", "sgemm_kernel")
+    return ("tc_gemm_kernel", "ssm_tc.cu", "tensor", 3 * 2.0 * Q * Q * N, "TFLOP/s",
+            "tc_gemm_kernel (fused update epilogue)" if fused else "tc_gemm_kernel")
 
 
 # --------------------------------------------------------------------------------------
@@ -312,7 +318,9 @@ def bench_ours(args):
                                           "||z-f|| and ||dz|| relative to ||z||")}
         results[key] = rec
         if (form, prec) == head:
-            kname, kfile, bound, amount, unit = dominant_kernel(form, prec, Q, N, info["rank"])
+            fused = bool(rec.get("launch", {}).get("tc_fused", 0))
+            kname, kfile, bound, amount, unit, tkey = dominant_kernel(form, prec, Q, N,
+                                                                      info["rank"], fused)
             avg_s = kms / max(kl, 1) / 1e3
             pk = measured_peaks()
             if bound == "hbm":
@@ -329,10 +337,10 @@ def bench_ours(args):
                 peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
                 achieved = amount / avg_s / 1e12
                 peak_src = "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"
-            traffic = traffic_record(kfile, kname)
+            traffic = traffic_record(kfile, tkey)
             headline = {
                 "rec": rec, "clocks": clk, "launches": launches,
-                "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
+                "roofline": {"bound": bound, "kernel": tkey, "achieved": achieved, "peak": peak,
                              "unit": unit, "frac": achieved / peak, "peak_source": peak_src,
                              "traffic": traffic,
                              "algorithmic_per_launch": amount},

@@ -102,8 +102,14 @@ struct TcArgs {
   float beta, xi, lam_s, inv_xb;
 };
 
-// compartments per load group of the fused epilogue (reads in flight per thread)
-constexpr int UG = 8;   // one tcgen05.ld of 8 columns and one 16-byte store of w each
+// compartments per load group of the fused epilogue: one tcgen05.ld of 8 columns and
+// one 16-byte store of w each
+constexpr int UG = 8;
+// groups whose reads are in flight at once per thread: two (software-pipelined) with up
+// to two neighbour rows per element; one with four (3D grids), whose reads would not fit
+// twice in registers
+template <int NRT>
+constexpr int pipe_depth() { return NRT == 4 ? 1 : 2; }
 
 // epilogue modes of tc_gemm_kernel
 constexpr int EPI_STORE = 0;         // acc -> Acc
@@ -165,20 +171,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 8 consecutive FP32 columns of this warp's 32 TMEM lanes
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+// 8 (or 4) consecutive FP32 columns of this warp's 32 TMEM lanes
+template <int C>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float* v) {
+  static_assert(C == 4 || C == 8, "columns");
   uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
+  if constexpr (C == 8) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr));
+  } else {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+  }
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < C; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int BN, int EPI>
+// NRT: staged neighbour rows the fused epilogue reads per element (2: 1D/2D grids and
+// stacked slices, 4: 3D grids); the store epilogue ignores it
+template <int BN, int EPI, int NRT>
 __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant__ TcMaps maps,
                                                           const TcArgs a) {
   constexpr int NS = Tile<BN>::NS, STAGE_BYTES = Tile<BN>::STAGE_BYTES;
@@ -329,60 +345,93 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
           nok[j] = j < NR && flags[j];
           dk[j] = nok[j] ? off[j] : 0;
         }
-        const int dxm = hxm ? -1 : 0, dxp = hxp ? 1 : 0;
         // groups of UG compartments of voxel n: a group's loads (coalesced across the
         // warp's 32 voxels; the neighbours are L1/L2 hits) are issued before its stores
         const DenseStep step{a.xi, a.lam_s, a.beta, a.inv_xb};
-#pragma unroll 1
-        for (int cg = half; cg < BN / UG; cg += NEPI / 4) {
+        // The warp's groups cg = half, half + NEPI/4, ... are software-pipelined over two
+        // register buffers (1D/2D grids): the loads of the next group are issued before
+        // the current group is computed, so two groups' reads are in flight. x neighbours
+        // come from the adjacent lanes (shuffles); the two values beyond the warp's 32
+        // voxels of each compartment are one register per group (lanes 0 .. UG-1: voxel
+        // n0w - 1, lanes UG .. 2 UG - 1: n0w + 32, for compartments q0 .. q0 + UG - 1);
+        // on 3D grids a single buffer, and x neighbours loaded (L1 hits).
+        constexpr int GS = NEPI / 4;
+        const int64_t n0w = n - lane;
+        // x neighbours: shuffles where the two-buffer pipeline needs the registers (1D/2D),
+        // L1-hit loads otherwise (3D)
+        constexpr bool XSHFL = pipe_depth<NRT>() == 2;
+        const int dxm = hxm ? -1 : 0, dxp = hxp ? 1 : 0;
+        struct Buf {
+          float z[UG], d[UG], h[UG], zk[NRT][UG], xm[UG], xp[UG], edge;
+        };
+        auto have = [&](int cg) { return cg < BN / UG && qt * BN + cg * UG < a.Q; };
+        auto load = [&](int cg, Buf& b) {
           const int q0 = qt * BN + cg * UG;
-          if (q0 >= a.Q) break;                     // uniform across the warp
+#pragma unroll
+          for (int j = 0; j < UG; ++j) {
+            // a padding column reads the last compartment's row (in bounds), unused;
+            // absent neighbours read the voxel's own value and are dropped
+            const int64_t o = (int64_t)min(q0 + j, a.Q - 1) * ld + n;
+            b.z[j] = __ldg(a.Zin + o);
+            b.d[j] = __ldg(a.Din + o);
+            b.h[j] = __ldg(a.H + o);
+#pragma unroll
+            for (int k = 0; k < NRT; ++k) b.zk[k][j] = __ldg(a.Zin + o + dk[k]);
+            if constexpr (!XSHFL) {
+              b.xm[j] = __ldg(a.Zin + o + dxm);
+              b.xp[j] = __ldg(a.Zin + o + dxp);
+            }
+          }
+          if constexpr (XSHFL) {
+            const int je = lane % UG, side = lane / UG;
+            const int64_t ne = side == 0 ? (n0w > 0 ? n0w - 1 : n0w)
+                                         : side == 1 ? min(n0w + 32, ld - 1) : n0w;
+            b.edge = __ldg(a.Zin + (int64_t)min(q0 + je, a.Q - 1) * ld + ne);
+          }
+        };
+        auto process = [&](int cg, Buf& b) {
+          const int q0 = qt * BN + cg * UG;
           float v[UG];
-          tmem_ld8(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 256 + cg * UG),
-                   v);
-          if (in) {
-            // every load of the group is issued before any arithmetic: absent neighbours
-            // read the voxel's own value (a valid address) and are dropped by selects
-            float zz[UG], dd[UG], hv[UG], nbv[UG];
+          tmem_ld_cols<UG>(
+              tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 256 + cg * UG), v);
 #pragma unroll
-            for (int j = 0; j < UG; ++j) {
-              // a padding column reads the last compartment's row (in bounds), unused
-              const int64_t o = (int64_t)min(q0 + j, a.Q - 1) * ld + n;
-              zz[j] = __ldg(a.Zin + o);
-              dd[j] = __ldg(a.Din + o);
-              hv[j] = __ldg(a.H + o);
-              const float zxm = __ldg(a.Zin + o + dxm), zxp = __ldg(a.Zin + o + dxp);
-              float zk[4];
-#pragma unroll
-              for (int k = 0; k < 4; ++k) zk[k] = k < NR ? __ldg(a.Zin + o + dk[k]) : 0.f;
-              float nb = 0.f;
-              nb += hxm ? zxm : 0.f;
-              nb += hxp ? zxp : 0.f;
-#pragma unroll
-              for (int k = 0; k < 4; ++k) nb += nok[k] ? zk[k] : 0.f;
-              nbv[j] = nb;
+          for (int j = 0; j < UG; ++j) {
+            float zl, zr;
+            if constexpr (XSHFL) {
+              zl = __shfl_up_sync(0xffffffffu, b.z[j], 1);
+              zr = __shfl_down_sync(0xffffffffu, b.z[j], 1);
+              const float el = __shfl_sync(0xffffffffu, b.edge, j);
+              const float er = __shfl_sync(0xffffffffu, b.edge, UG + j);
+              if (lane == 0) zl = el;
+              if (lane == 31) zr = er;
+            } else {
+              zl = b.xm[j];
+              zr = b.xp[j];
             }
-            uint32_t hh[UG / 2], ll[UG / 2];
+            float nb = 0.f;
+            nb += hxm ? zl : 0.f;
+            nb += hxp ? zr : 0.f;
 #pragma unroll
-            for (int j = 0; j < UG; ++j) {
-              const int q = q0 + j;
-              float w = 0.f;                        // padding columns stay zero
-              if (q < a.Q) {
-                const int64_t o = (int64_t)q * ld + n;
-                const float f = __fadd_rn(hv[j], v[j]);
-                float dn;
-                const float zn = step.apply(zz[j], dd[j], f, deg, nbv[j], dn, w);
-                a.Zout[o] = zn;
-                a.Dout[o] = dn;
-                if constexpr (EPI == EPI_UPDATE_CHECK) {
-                  const float e = zn - f, ch = zn - zz[j];
-                  s1 = fmaf(e, e, s1);
-                  s2 = fmaf(ch, ch, s2);
-                  s3 = fmaf(zn, zn, s3);
-                }
+            for (int k = 0; k < NRT; ++k) nb += nok[k] ? b.zk[k][j] : 0.f;
+            const int q = q0 + j;
+            const float f = __fadd_rn(b.h[j], v[j]);
+            float dn, w;
+            const float zn = step.apply(b.z[j], b.d[j], f, deg, nb, dn, w);
+            if (in && q < a.Q) {
+              const int64_t o = (int64_t)q * ld + n;
+              a.Zout[o] = zn;
+              a.Dout[o] = dn;
+              if constexpr (EPI == EPI_UPDATE_CHECK) {
+                const float e = zn - f, ch = zn - b.z[j];
+                s1 = fmaf(e, e, s1);
+                s2 = fmaf(ch, ch, s2);
+                s3 = fmaf(zn, zn, s3);
               }
-              v[j] = w;
             }
+            v[j] = q < a.Q ? w : 0.f;               // padding columns stay zero
+          }
+          if (in) {
+            uint32_t hh[UG / 2], ll[UG / 2];
 #pragma unroll
             for (int e = 0; e < UG / 2; ++e) {
               const float w0 = v[2 * e], w1 = v[2 * e + 1];
@@ -394,6 +443,28 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
             *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
           }
           __syncwarp();
+        };
+        if constexpr (pipe_depth<NRT>() == 2) {
+          Buf b0, b1;
+          int cg = half;
+          if (have(cg)) load(cg, b0);
+#pragma unroll 1
+          while (have(cg)) {
+            if (have(cg + GS)) load(cg + GS, b1);
+            process(cg, b0);
+            cg += GS;
+            if (!have(cg)) break;
+            if (have(cg + GS)) load(cg + GS, b0);
+            process(cg, b1);
+            cg += GS;
+          }
+        } else {
+          Buf b0;
+#pragma unroll 1
+          for (int cg = half; have(cg); cg += GS) {
+            load(cg, b0);
+            process(cg, b0);
+          }
         }
       } else
       for (int cc = half; cc < BN / 32; cc += NEPI / 4) {
@@ -451,7 +522,7 @@ int gemm_grid(const ssm_plan_s* pl, int bn) {
   return std::max(1, std::min(sm_count() * std::max(1, pl->waves), ntv * ntq));
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, int NRT>
 ssm_status launch_gemm(const ssm_plan_s* pl, int cur, double* partial, cudaStream_t s) {
   const uint64_t Q = (uint64_t)pl->Q, N = (uint64_t)pl->g.N, Qp = (uint64_t)pl->Qp;
   TcMaps m;
@@ -482,23 +553,34 @@ ssm_status launch_gemm(const ssm_plan_s* pl, int cur, double* partial, cudaStrea
   a.xi = (float)pl->xi;
   a.lam_s = (float)pl->lam_s;
   a.inv_xb = (float)(1.0 / (pl->xi + pl->p.beta));
-  tc_gemm_kernel<BN, EPI><<<gemm_grid(pl, BN), NTHR, Tile<BN>::SMEM_BYTES, s>>>(m, a);
+  tc_gemm_kernel<BN, EPI, NRT><<<gemm_grid(pl, BN), NTHR, Tile<BN>::SMEM_BYTES, s>>>(m, a);
   SSM_LAUNCHED();
   return SSM_OK;
 }
 
-template <int EPI>
-ssm_status gemm_dispatch(const ssm_plan_s* pl, int bn, int cur, double* partial, cudaStream_t s) {
+// staged neighbour rows of the plan's grid: 4 on 3D grids, else at most 2
+int fused_nrt(const ssm_plan_s* pl) { return pl->g.ny > 1 && pl->g.nz > 1 && pl->g.zlink ? 4 : 2; }
+
+template <int EPI, int NRT>
+ssm_status gemm_dispatch_n(const ssm_plan_s* pl, int bn, int cur, double* partial, cudaStream_t s) {
   switch (bn) {
-    case 256: return launch_gemm<256, EPI>(pl, cur, partial, s);
-    case 224: return launch_gemm<224, EPI>(pl, cur, partial, s);
-    case 192: return launch_gemm<192, EPI>(pl, cur, partial, s);
-    case 160: return launch_gemm<160, EPI>(pl, cur, partial, s);
-    case 128: return launch_gemm<128, EPI>(pl, cur, partial, s);
+    case 256: return launch_gemm<256, EPI, NRT>(pl, cur, partial, s);
+    case 224: return launch_gemm<224, EPI, NRT>(pl, cur, partial, s);
+    case 192: return launch_gemm<192, EPI, NRT>(pl, cur, partial, s);
+    case 160: return launch_gemm<160, EPI, NRT>(pl, cur, partial, s);
+    case 128: return launch_gemm<128, EPI, NRT>(pl, cur, partial, s);
     default:
       set_error("tensor-core GEMM: unsupported tile width");
       return SSM_EUNSUPPORTED;
   }
+}
+
+template <int EPI>
+ssm_status gemm_dispatch(const ssm_plan_s* pl, int bn, int cur, double* partial, cudaStream_t s) {
+  if constexpr (EPI != EPI_STORE) {
+    if (fused_nrt(pl) == 4) return gemm_dispatch_n<EPI, 4>(pl, bn, cur, partial, s);
+  }
+  return gemm_dispatch_n<EPI, 2>(pl, bn, cur, partial, s);
 }
 
 ssm_status gemm_dispatch(const ssm_plan_s* pl, int bn, int cur, cudaStream_t s) {
@@ -507,9 +589,11 @@ ssm_status gemm_dispatch(const ssm_plan_s* pl, int bn, int cur, cudaStream_t s) 
 
 template <int BN>
 cudaError_t set_smem_attr() {
-  for (const void* k : {(const void*)tc_gemm_kernel<BN, EPI_STORE>,
-                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE>,
-                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE_CHECK>}) {
+  for (const void* k : {(const void*)tc_gemm_kernel<BN, EPI_STORE, 2>,
+                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE, 2>,
+                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE_CHECK, 2>,
+                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE, 4>,
+                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE_CHECK, 4>}) {
     const cudaError_t e =
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::SMEM_BYTES);
     if (e != cudaSuccess) return e;
