@@ -303,9 +303,11 @@ typedef struct {
                               iteration only)                                       */
   int lowrank_grid;        /* CTAs of the fused low-rank kernel                      */
   int sm_count;            /* SMs of the plan's device                               */
-  int tc_fused;            /* 1: the tensor-core iteration is one kernel (the update
-                              in the GEMM's epilogue); 0: GEMM + update kernel. Chosen
-                              at plan time by timing both; results are identical    */
+  int tc_fused;            /* tensor-core iteration: 0 = GEMM + update kernel; 1 = one
+                              kernel, the update in the GEMM's epilogue with its reads
+                              staged in shared memory by TMA; 2 = one kernel, reads
+                              pipelined in registers. Chosen at plan time by timing
+                              the candidates; results are identical                 */
 } ssm_launch_info;
 
 ssm_status ssm_plan_launch_info(ssm_plan_t plan, ssm_launch_info* out);

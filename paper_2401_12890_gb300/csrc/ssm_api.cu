@@ -1038,10 +1038,10 @@ ssm_status ssm_plan_launch_info(ssm_plan_t plan, ssm_launch_info* out) {
   if (plan->p.form == SSM_FORM_LOWRANK) {
     out->lowrank_grid = (int)plan->lr_grid;
   } else if (plan->Whi[0]) {
-    out->gemm_tile_n = plan->tc_bn;
+    out->gemm_tile_n = tc_tile_width(plan);
     out->gemm_grid = tc_gemm_grid(plan);
     out->update_grid = tc_update_grid(plan);
-    out->tc_fused = plan->tc_fused ? 1 : 0;
+    out->tc_fused = plan->tc_fused ? (plan->tc_fused_reg ? 2 : 1) : 0;
   }
   return SSM_OK;
 }

@@ -171,7 +171,9 @@ struct ssm_plan_s {
   int waves = 1;
   // compartment-tile width of the tensor-core GEMM (chosen by its autotuner)
   int tc_bn = 256;
-  bool tc_fused = true;         // tensor-core form: one fused GEMM + update kernel per iteration
+  int tc_bn_fused = 0;          // tile width of the fused iteration kernel (0: none fits)
+  bool tc_fused = false;        // tensor-core form: one fused GEMM + update kernel per iteration
+  bool tc_fused_reg = false;    // ... with the register epilogue (else the staged one)
   // Algorithm 1 (SSM_FORM_ADMM): state, per-axis DCT matrices (forward, inverse), scaling
   ssm::AdmmState adm{};
   float* adm_T[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
@@ -249,5 +251,6 @@ ssm_status tc_update(ssm_plan_s* pl, int cur, bool check, double* partial, int* 
 void tc_release(ssm_plan_s* pl);
 int tc_max_partials(const ssm_plan_s* pl);
 int tc_gemm_grid(const ssm_plan_s* pl);
+int tc_tile_width(const ssm_plan_s* pl);
 
 }  // namespace ssm

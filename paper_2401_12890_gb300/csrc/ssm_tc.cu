@@ -36,6 +36,7 @@
 // next tile's MMAs. Every mbarrier wait is bounded.
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <tuple>
 
@@ -53,7 +54,8 @@ constexpr int BM = 128;                         // voxels per tile (MMA M, TMEM 
 constexpr int BK = 64;                          // K per stage: one 128-byte swizzle atom
 constexpr int UK = 16;                          // K per tcgen05.mma (kind::f16)
 constexpr int NEPI = SSM_TC_NEPI;                // epilogue warps (2 per TMEM lane quarter)
-constexpr int NTHR = 64 + 32 * NEPI;            // TMA warp, MMA warp, epilogue warps
+constexpr int EPW = 2 + NEPI;                   // the fused epilogue's TMA producer warp
+constexpr int NTHR = 96 + 32 * NEPI;            // TMA, MMA, epilogue warps, epilogue TMA
 constexpr uint32_t TMEM_COLS = 512;             // two accumulators, at columns 0 and 256
 constexpr int A_BYTES = BM * BK * 2;            // 16 KB
 constexpr int kSmemLimit = 227 * 1024;
@@ -70,7 +72,6 @@ struct Tile {
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int NS = (kSmemLimit - 2048) / STAGE_BYTES > 4 ? 4
                                                                   : (kSmemLimit - 2048) / STAGE_BYTES;
-  static constexpr int SMEM_BYTES = NS * STAGE_BYTES + 1024 + 256;
   // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9,
   // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
@@ -81,6 +82,9 @@ struct Tile {
 struct TcMaps {
   CUtensorMap a_hi, a_lo;   // w (voxel-major), box {BK, BM}
   CUtensorMap b_hi, b_lo;   // M, box {BK, BN}
+  // fused epilogue (map-major Q x N arrays): z with its x halo {EZW, UG}, z neighbour
+  // rows {ENW, UG}, d and h {BM, UG}
+  CUtensorMap ez_c, ez_n, ed, eh;
 };
 
 struct TcArgs {
@@ -102,19 +106,65 @@ struct TcArgs {
   float beta, xi, lam_s, inv_xb;
 };
 
-// compartments per load group of the fused epilogue: one tcgen05.ld of 8 columns and
-// one 16-byte store of w each
+// compartments per group of the fused epilogue: one tcgen05.ld of 8 columns and one
+// 16-byte store of w each
 constexpr int UG = 8;
-// groups whose reads are in flight at once per thread: two (software-pipelined) with up
-// to two neighbour rows per element; one with four (3D grids), whose reads would not fit
-// twice in registers
-template <int NRT>
-constexpr int pipe_depth() { return NRT == 4 ? 1 : 2; }
-
 // epilogue modes of tc_gemm_kernel
 constexpr int EPI_STORE = 0;         // acc -> Acc
-constexpr int EPI_UPDATE = 1;        // the element-wise steps of the iteration
+constexpr int EPI_UPDATE = 1;        // the element-wise steps of the iteration, reads staged
+                                     // in shared memory by TMA
 constexpr int EPI_UPDATE_CHECK = 2;  // ... plus the residual sums of the stopping rule
+constexpr int EPI_REG = 3;           // the element-wise steps, reads software-pipelined in
+                                     // registers (no shared memory: any tile width)
+constexpr int EPI_REG_CHECK = 4;     // ... plus the residual sums
+constexpr bool epi_check(int e) { return e == EPI_UPDATE_CHECK || e == EPI_REG_CHECK; }
+constexpr bool epi_staged(int e) { return e == EPI_UPDATE || e == EPI_UPDATE_CHECK; }
+
+// register epilogue: groups whose reads are in flight at once per thread -- two
+// (software-pipelined) with up to two neighbour rows per element, one with four (3D)
+template <int NRT>
+constexpr int pipe_depth() { return NRT == 4 ? 1 : 2; }
+constexpr int EZW = BM + 8;   // staged z row: voxels n0-4 .. n0+BM+3 (the x halo)
+constexpr int ENW = BM + 4;   // staged neighbour row: 4-aligned base .. +BM+3
+
+// One stage of the fused epilogue's ring: a group of UG compartments of a voxel tile --
+// z with its x halo, NRT neighbour rows (the -+nx, -+nx*ny rows), d and h -- each a TMA
+// box (128-byte-aligned offsets).
+template <int NRT>
+struct EpiStage {
+  static constexpr int zc = 0;
+  static constexpr int zn = UG * EZW * 4;
+  static constexpr int dd = zn + NRT * UG * ENW * 4;
+  static constexpr int hh = dd + UG * BM * 4;
+  static constexpr int bytes = hh + UG * BM * 4;
+  static_assert(zn % 128 == 0 && dd % 128 == 0 && hh % 128 == 0 && bytes % 128 == 0, "layout");
+};
+
+// Shared memory of one kernel configuration. The store epilogue gives the GEMM's operand
+// ring all of it; the fused epilogue keeps the ring at 2 stages and fills the rest with
+// 2 or 4 epilogue stages. A fused configuration needs 2 of them: BN <= 224 on grids with
+// 2 neighbour rows, BN <= 192 on 3D grids.
+template <int BN, int EPI, int NRT>
+struct Cfg {
+  static constexpr bool fused = epi_staged(EPI);   // an epilogue ring in shared memory
+  static constexpr int NS = fused ? 2 : Tile<BN>::NS;
+  static constexpr int RESERVE = 1024 + 256;    // alignment slack, barriers, TMEM slot
+  static constexpr int EST = EpiStage<NRT>::bytes;
+  static constexpr int room = kSmemLimit - RESERVE - NS * Tile<BN>::STAGE_BYTES;
+  // an even number of stages: slot = sequence index mod NBE then has the parity of the
+  // sequence index, so every slot is consumed by one half of the epilogue warps and its
+  // barrier phases complete in that half's order (with an odd count the halves would
+  // alternate on a slot, and a half waiting by parity could pass on an older phase)
+  static constexpr int NBE = fused ? ((room / EST > 4 ? 4 : room / EST) & ~1) : 0;
+  static constexpr bool valid = !fused || NBE >= 2;
+  static constexpr int SMEM_BYTES = NS * Tile<BN>::STAGE_BYTES + NBE * EST + RESERVE;
+};
+
+
+// round down to a multiple of 4 (toward -infinity): a 16-byte-aligned TMA x coordinate
+__host__ __device__ __forceinline__ int64_t floor4i(int64_t v) {
+  return v >= 0 ? (v & ~(int64_t)3) : -(((-v) + 3) & ~(int64_t)3);
+}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
@@ -197,17 +247,23 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float* v) {
 template <int BN, int EPI, int NRT>
 __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant__ TcMaps maps,
                                                           const TcArgs a) {
-  constexpr int NS = Tile<BN>::NS, STAGE_BYTES = Tile<BN>::STAGE_BYTES;
+  using C = Cfg<BN, EPI, NRT>;
+  using ES = EpiStage<NRT>;
+  constexpr int NS = C::NS, NBE = C::NBE, STAGE_BYTES = Tile<BN>::STAGE_BYTES;
   constexpr int B_BYTES = Tile<BN>::B_BYTES;
   constexpr uint32_t IDESC = Tile<BN>::IDESC;
+  static_assert(C::valid, "fused epilogue needs two ring stages");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * STAGE_BYTES);
+  unsigned char* estage = smem + NS * STAGE_BYTES;      // the epilogue ring (fused)
+  uint64_t* full = reinterpret_cast<uint64_t*>(estage + NBE * C::EST);
   uint64_t* empty = full + NS;
   uint64_t* tfull = empty + NS;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* efull = tempty + 2;     // epilogue stage loaded
+  uint64_t* eempty = efull + 4;     // epilogue stage consumed (4 warps: one half)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(eempty + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
@@ -218,6 +274,10 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], NEPI);
+    }
+    for (int i = 0; i < NBE; ++i) {
+      mbar_init(&efull[i], 1);
+      mbar_init(&eempty[i], NEPI / 2);
     }
     mbar_fence_init();
   }
@@ -258,6 +318,45 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
           tma_load_2d(st + A_BYTES, &maps.a_lo, kc * BK, vt * BM, &full[s]);
           tma_load_2d(st + 2 * A_BYTES, &maps.b_hi, kc * BK, qt * BN, &full[s]);
           tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.b_lo, kc * BK, qt * BN, &full[s]);
+        }
+      }
+    }
+  } else if (warp == EPW) {
+    // ------------------------------------------------------------ epilogue TMA producer
+    // streams each (tile, group) of the CTA's sequence into the epilogue ring, running
+    // up to NBE groups ahead of the epilogue warps (these reads do not depend on the MMAs)
+    if constexpr (C::fused) {
+      if (lane == 0) {
+        const int nx = a.g.nx, ny = a.g.ny;
+        const bool zl = a.g.nz > 1 && a.g.zlink;
+        const int NR = (ny > 1 ? 2 : 0) + (zl ? 2 : 0);
+        const int64_t plane = (int64_t)nx * ny;
+        const int64_t off[4] = {ny > 1 ? -(int64_t)nx : -plane, ny > 1 ? (int64_t)nx : plane,
+                                -plane, plane};
+        const unsigned bytes = (unsigned)((UG * EZW + NR * UG * ENW + 2 * UG * BM) * 4);
+        tma_prefetch_map(&maps.ez_c);
+        tma_prefetch_map(&maps.ez_n);
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+          const int vt = t / a.ntq, qt = t % a.ntq;
+          const int64_t n0 = (int64_t)vt * BM;
+          for (int cg = 0; cg < BN / UG; ++cg, ++i) {
+            const int q0 = qt * BN + cg * UG;
+            if (q0 >= a.Q) break;
+            const int slot = i % NBE, k = i / NBE;
+            if (k > 0 && !mbar_wait(&eempty[slot], (k - 1) & 1)) {
+              failed = true;
+              break;
+            }
+            unsigned char* st = estage + slot * C::EST;
+            mbar_arrive_expect_tx(&efull[slot], bytes);
+            tma_load_2d(st + ES::zc, &maps.ez_c, (int)(n0 - 4), q0, &efull[slot]);
+            for (int j = 0; j < NR; ++j)
+              tma_load_2d(st + ES::zn + j * UG * ENW * 4, &maps.ez_n,
+                          (int)floor4i(n0 + off[j]), q0, &efull[slot]);
+            tma_load_2d(st + ES::dd, &maps.ed, (int)n0, q0, &efull[slot]);
+            tma_load_2d(st + ES::hh, &maps.eh, (int)n0, q0, &efull[slot]);
+          }
         }
       }
     }
@@ -311,8 +410,11 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
     const int64_t off[4] = {ny > 1 ? -(int64_t)nx : -plane, ny > 1 ? (int64_t)nx : plane,
                             -plane, plane};
     int it = 0;
+    int gseq = 0;   // position in the CTA's sequence of (tile, group) (fused epilogue)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       const int acc = it & 1, ra = it >> 1;
+      // every epilogue warp waits for each tile's accumulator (also one whose half has no
+      // group in the tile), so no warp's release of an accumulator runs a phase ahead
       if (!failed && !mbar_wait(&tfull[acc], ra & 1)) failed = true;
       tc_fence_after();
       const int vt = t / a.ntq, qt = t % a.ntq;
@@ -338,132 +440,205 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
         const bool hzp = zl && in && zc < nz - 1 && (!mk || mk[n + plane]);
         const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
         const bool flags[4] = {ny > 1 ? hym : hzm, ny > 1 ? hyp : hzp, hzm, hzp};
-        bool nok[4];
-        int64_t dk[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          nok[j] = j < NR && flags[j];
-          dk[j] = nok[j] ? off[j] : 0;
-        }
-        // groups of UG compartments of voxel n: a group's loads (coalesced across the
-        // warp's 32 voxels; the neighbours are L1/L2 hits) are issued before its stores
-        const DenseStep step{a.xi, a.lam_s, a.beta, a.inv_xb};
-        // The warp's groups cg = half, half + NEPI/4, ... are software-pipelined over two
-        // register buffers (1D/2D grids): the loads of the next group are issued before
-        // the current group is computed, so two groups' reads are in flight. x neighbours
-        // come from the adjacent lanes (shuffles); the two values beyond the warp's 32
-        // voxels of each compartment are one register per group (lanes 0 .. UG-1: voxel
-        // n0w - 1, lanes UG .. 2 UG - 1: n0w + 32, for compartments q0 .. q0 + UG - 1);
-        // on 3D grids a single buffer, and x neighbours loaded (L1 hits).
-        constexpr int GS = NEPI / 4;
-        const int64_t n0w = n - lane;
-        // x neighbours: shuffles where the two-buffer pipeline needs the registers (1D/2D),
-        // L1-hit loads otherwise (3D)
-        constexpr bool XSHFL = pipe_depth<NRT>() == 2;
-        const int dxm = hxm ? -1 : 0, dxp = hxp ? 1 : 0;
-        struct Buf {
-          float z[UG], d[UG], h[UG], zk[NRT][UG], xm[UG], xp[UG], edge;
-        };
-        auto have = [&](int cg) { return cg < BN / UG && qt * BN + cg * UG < a.Q; };
-        auto load = [&](int cg, Buf& b) {
-          const int q0 = qt * BN + cg * UG;
-#pragma unroll
-          for (int j = 0; j < UG; ++j) {
-            // a padding column reads the last compartment's row (in bounds), unused;
-            // absent neighbours read the voxel's own value and are dropped
-            const int64_t o = (int64_t)min(q0 + j, a.Q - 1) * ld + n;
-            b.z[j] = __ldg(a.Zin + o);
-            b.d[j] = __ldg(a.Din + o);
-            b.h[j] = __ldg(a.H + o);
-#pragma unroll
-            for (int k = 0; k < NRT; ++k) b.zk[k][j] = __ldg(a.Zin + o + dk[k]);
-            if constexpr (!XSHFL) {
-              b.xm[j] = __ldg(a.Zin + o + dxm);
-              b.xp[j] = __ldg(a.Zin + o + dxp);
-            }
+        if constexpr (epi_staged(EPI)) {
+          bool nok[4];
+          int rem[4];   // staged neighbour row k holds voxel v at index v + rem[k]
+          const int64_t n0 = (int64_t)vt * BM;
+  #pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            nok[j] = j < NR && flags[j];
+            rem[j] = (int)(n0 + off[j] - floor4i(n0 + off[j]));
           }
-          if constexpr (XSHFL) {
-            const int je = lane % UG, side = lane / UG;
-            const int64_t ne = side == 0 ? (n0w > 0 ? n0w - 1 : n0w)
-                                         : side == 1 ? min(n0w + 32, ld - 1) : n0w;
-            b.edge = __ldg(a.Zin + (int64_t)min(q0 + je, a.Q - 1) * ld + ne);
-          }
-        };
-        auto process = [&](int cg, Buf& b) {
-          const int q0 = qt * BN + cg * UG;
-          float v[UG];
-          tmem_ld_cols<UG>(
-              tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 256 + cg * UG), v);
-#pragma unroll
-          for (int j = 0; j < UG; ++j) {
-            float zl, zr;
-            if constexpr (XSHFL) {
-              zl = __shfl_up_sync(0xffffffffu, b.z[j], 1);
-              zr = __shfl_down_sync(0xffffffffu, b.z[j], 1);
-              const float el = __shfl_sync(0xffffffffu, b.edge, j);
-              const float er = __shfl_sync(0xffffffffu, b.edge, UG + j);
-              if (lane == 0) zl = el;
-              if (lane == 31) zr = er;
-            } else {
-              zl = b.xm[j];
-              zr = b.xp[j];
-            }
-            float nb = 0.f;
-            nb += hxm ? zl : 0.f;
-            nb += hxp ? zr : 0.f;
-#pragma unroll
-            for (int k = 0; k < NRT; ++k) nb += nok[k] ? b.zk[k][j] : 0.f;
-            const int q = q0 + j;
-            const float f = __fadd_rn(b.h[j], v[j]);
-            float dn, w;
-            const float zn = step.apply(b.z[j], b.d[j], f, deg, nb, dn, w);
-            if (in && q < a.Q) {
-              const int64_t o = (int64_t)q * ld + n;
-              a.Zout[o] = zn;
-              a.Dout[o] = dn;
-              if constexpr (EPI == EPI_UPDATE_CHECK) {
-                const float e = zn - f, ch = zn - b.z[j];
-                s1 = fmaf(e, e, s1);
-                s2 = fmaf(ch, ch, s2);
-                s3 = fmaf(zn, zn, s3);
+          const DenseStep step{a.xi, a.lam_s, a.beta, a.inv_xb};
+          // the tile's groups of UG compartments in the CTA's sequence (the order the
+          // epilogue producer stages them): this warp's half takes every other one
+          for (int cg = 0; cg < BN / UG; ++cg, ++gseq) {
+            const int q0 = qt * BN + cg * UG;
+            if (q0 >= a.Q) break;                     // uniform across the warp
+            if ((gseq & 1) != half) continue;
+            const int slot = gseq % NBE, k = gseq / NBE;
+            if (!failed && !mbar_wait(&efull[slot], k & 1)) failed = true;
+            float v[UG];
+            tmem_ld_cols<UG>(
+                tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 256 + cg * UG), v);
+            const unsigned char* st = estage + slot * C::EST;
+            const float* zc_ = reinterpret_cast<const float*>(st + ES::zc);
+            const float* zn_ = reinterpret_cast<const float*>(st + ES::zn);
+            const float* dd_ = reinterpret_cast<const float*>(st + ES::dd);
+            const float* hh_ = reinterpret_cast<const float*>(st + ES::hh);
+            if (!failed) {
+  #pragma unroll
+              for (int j = 0; j < UG; ++j) {
+                const float z = zc_[j * EZW + 4 + row];
+                float nb = 0.f;
+                nb += hxm ? zc_[j * EZW + 3 + row] : 0.f;
+                nb += hxp ? zc_[j * EZW + 5 + row] : 0.f;
+  #pragma unroll
+                for (int kk = 0; kk < NRT; ++kk)
+                  nb += nok[kk] ? zn_[(kk * UG + j) * ENW + row + rem[kk]] : 0.f;
+                const int q = q0 + j;
+                const float f = __fadd_rn(hh_[j * BM + row], v[j]);
+                float dn, w;
+                const float zn = step.apply(z, dd_[j * BM + row], f, deg, nb, dn, w);
+                if (in && q < a.Q) {
+                  const int64_t o = (int64_t)q * ld + n;
+                  a.Zout[o] = zn;
+                  a.Dout[o] = dn;
+                  if constexpr (epi_check(EPI)) {
+                    const float e = zn - f, ch = zn - z;
+                    s1 = fmaf(e, e, s1);
+                    s2 = fmaf(ch, ch, s2);
+                    s3 = fmaf(zn, zn, s3);
+                  }
+                }
+                v[j] = q < a.Q ? w : 0.f;             // padding columns stay zero
+              }
+              if (in) {
+                uint32_t hh[UG / 2], ll[UG / 2];
+  #pragma unroll
+                for (int e = 0; e < UG / 2; ++e) {
+                  const float w0 = v[2 * e], w1 = v[2 * e + 1];
+                  hh[e] = pack_bf16x2(w0, w1);
+                  ll[e] = pack_bf16x2(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
+                                      w1 - __bfloat162float(__float2bfloat16_rn(w1)));
+                }
+                *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0) =
+                    make_uint4(hh[0], hh[1], hh[2], hh[3]);
+                *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0) =
+                    make_uint4(ll[0], ll[1], ll[2], ll[3]);
               }
             }
-            v[j] = q < a.Q ? w : 0.f;               // padding columns stay zero
-          }
-          if (in) {
-            uint32_t hh[UG / 2], ll[UG / 2];
-#pragma unroll
-            for (int e = 0; e < UG / 2; ++e) {
-              const float w0 = v[2 * e], w1 = v[2 * e + 1];
-              hh[e] = pack_bf16x2(w0, w1);
-              ll[e] = pack_bf16x2(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
-                                  w1 - __bfloat162float(__float2bfloat16_rn(w1)));
-            }
-            *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
-            *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
-          }
-          __syncwarp();
-        };
-        if constexpr (pipe_depth<NRT>() == 2) {
-          Buf b0, b1;
-          int cg = half;
-          if (have(cg)) load(cg, b0);
-#pragma unroll 1
-          while (have(cg)) {
-            if (have(cg + GS)) load(cg + GS, b1);
-            process(cg, b0);
-            cg += GS;
-            if (!have(cg)) break;
-            if (have(cg + GS)) load(cg + GS, b0);
-            process(cg, b1);
-            cg += GS;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&eempty[slot]);
           }
         } else {
-          Buf b0;
-#pragma unroll 1
-          for (int cg = half; have(cg); cg += GS) {
-            load(cg, b0);
-            process(cg, b0);
+          bool nok[4];
+          int64_t dk[4];
+  #pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            nok[j] = j < NR && flags[j];
+            dk[j] = nok[j] ? off[j] : 0;
+          }
+          // groups of UG compartments of voxel n: a group's loads (coalesced across the
+          // warp's 32 voxels; the neighbours are L1/L2 hits) are issued before its stores
+          const DenseStep step{a.xi, a.lam_s, a.beta, a.inv_xb};
+          // The warp's groups cg = half, half + NEPI/4, ... are software-pipelined over two
+          // register buffers (1D/2D grids): the loads of the next group are issued before
+          // the current group is computed, so two groups' reads are in flight. x neighbours
+          // come from the adjacent lanes (shuffles); the two values beyond the warp's 32
+          // voxels of each compartment are one register per group (lanes 0 .. UG-1: voxel
+          // n0w - 1, lanes UG .. 2 UG - 1: n0w + 32, for compartments q0 .. q0 + UG - 1);
+          // on 3D grids a single buffer, and x neighbours loaded (L1 hits).
+          constexpr int GS = NEPI / 4;
+          const int64_t n0w = n - lane;
+          // x neighbours: shuffles where the two-buffer pipeline needs the registers (1D/2D),
+          // L1-hit loads otherwise (3D)
+          constexpr bool XSHFL = pipe_depth<NRT>() == 2;
+          const int dxm = hxm ? -1 : 0, dxp = hxp ? 1 : 0;
+          struct Buf {
+            float z[UG], d[UG], h[UG], zk[NRT][UG], xm[UG], xp[UG], edge;
+          };
+          auto have = [&](int cg) { return cg < BN / UG && qt * BN + cg * UG < a.Q; };
+          auto load = [&](int cg, Buf& b) {
+            const int q0 = qt * BN + cg * UG;
+  #pragma unroll
+            for (int j = 0; j < UG; ++j) {
+              // a padding column reads the last compartment's row (in bounds), unused;
+              // absent neighbours read the voxel's own value and are dropped
+              const int64_t o = (int64_t)min(q0 + j, a.Q - 1) * ld + n;
+              b.z[j] = __ldg(a.Zin + o);
+              b.d[j] = __ldg(a.Din + o);
+              b.h[j] = __ldg(a.H + o);
+  #pragma unroll
+              for (int k = 0; k < NRT; ++k) b.zk[k][j] = __ldg(a.Zin + o + dk[k]);
+              if constexpr (!XSHFL) {
+                b.xm[j] = __ldg(a.Zin + o + dxm);
+                b.xp[j] = __ldg(a.Zin + o + dxp);
+              }
+            }
+            if constexpr (XSHFL) {
+              const int je = lane % UG, side = lane / UG;
+              const int64_t ne = side == 0 ? (n0w > 0 ? n0w - 1 : n0w)
+                                           : side == 1 ? min(n0w + 32, ld - 1) : n0w;
+              b.edge = __ldg(a.Zin + (int64_t)min(q0 + je, a.Q - 1) * ld + ne);
+            }
+          };
+          auto process = [&](int cg, Buf& b) {
+            const int q0 = qt * BN + cg * UG;
+            float v[UG];
+            tmem_ld_cols<UG>(
+                tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 256 + cg * UG), v);
+  #pragma unroll
+            for (int j = 0; j < UG; ++j) {
+              float zl, zr;
+              if constexpr (XSHFL) {
+                zl = __shfl_up_sync(0xffffffffu, b.z[j], 1);
+                zr = __shfl_down_sync(0xffffffffu, b.z[j], 1);
+                const float el = __shfl_sync(0xffffffffu, b.edge, j);
+                const float er = __shfl_sync(0xffffffffu, b.edge, UG + j);
+                if (lane == 0) zl = el;
+                if (lane == 31) zr = er;
+              } else {
+                zl = b.xm[j];
+                zr = b.xp[j];
+              }
+              float nb = 0.f;
+              nb += hxm ? zl : 0.f;
+              nb += hxp ? zr : 0.f;
+  #pragma unroll
+              for (int k = 0; k < NRT; ++k) nb += nok[k] ? b.zk[k][j] : 0.f;
+              const int q = q0 + j;
+              const float f = __fadd_rn(b.h[j], v[j]);
+              float dn, w;
+              const float zn = step.apply(b.z[j], b.d[j], f, deg, nb, dn, w);
+              if (in && q < a.Q) {
+                const int64_t o = (int64_t)q * ld + n;
+                a.Zout[o] = zn;
+                a.Dout[o] = dn;
+                if constexpr (epi_check(EPI)) {
+                  const float e = zn - f, ch = zn - b.z[j];
+                  s1 = fmaf(e, e, s1);
+                  s2 = fmaf(ch, ch, s2);
+                  s3 = fmaf(zn, zn, s3);
+                }
+              }
+              v[j] = q < a.Q ? w : 0.f;               // padding columns stay zero
+            }
+            if (in) {
+              uint32_t hh[UG / 2], ll[UG / 2];
+  #pragma unroll
+              for (int e = 0; e < UG / 2; ++e) {
+                const float w0 = v[2 * e], w1 = v[2 * e + 1];
+                hh[e] = pack_bf16x2(w0, w1);
+                ll[e] = pack_bf16x2(w0 - __bfloat162float(__float2bfloat16_rn(w0)),
+                                    w1 - __bfloat162float(__float2bfloat16_rn(w1)));
+              }
+              *reinterpret_cast<uint4*>(a.Whi + n * a.Qp + q0) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+              *reinterpret_cast<uint4*>(a.Wlo + n * a.Qp + q0) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+            }
+            __syncwarp();
+          };
+          if constexpr (pipe_depth<NRT>() == 2) {
+            Buf b0, b1;
+            int cg = half;
+            if (have(cg)) load(cg, b0);
+  #pragma unroll 1
+            while (have(cg)) {
+              if (have(cg + GS)) load(cg + GS, b1);
+              process(cg, b0);
+              cg += GS;
+              if (!have(cg)) break;
+              if (have(cg + GS)) load(cg + GS, b0);
+              process(cg, b1);
+              cg += GS;
+            }
+          } else {
+            Buf b0;
+  #pragma unroll 1
+            for (int cg = half; have(cg); cg += GS) {
+              load(cg, b0);
+              process(cg, b0);
+            }
           }
         }
       } else
@@ -486,7 +661,7 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
     }
   }
   if (failed) atomicExch(a.err, (int)SSM_ETIMEOUT);
-  if constexpr (EPI == EPI_UPDATE_CHECK) {
+  if constexpr (epi_check(EPI)) {
     double d1 = s1, d2 = s2, d3 = s3;
     for (int o = 16; o > 0; o >>= 1) {
       d1 += __shfl_xor_sync(0xffffffffu, d1, o);
@@ -525,13 +700,23 @@ int gemm_grid(const ssm_plan_s* pl, int bn) {
 template <int BN, int EPI, int NRT>
 ssm_status launch_gemm(const ssm_plan_s* pl, int cur, double* partial, cudaStream_t s) {
   const uint64_t Q = (uint64_t)pl->Q, N = (uint64_t)pl->g.N, Qp = (uint64_t)pl->Qp;
+  using C = Cfg<BN, EPI, NRT>;
   TcMaps m;
+  std::memset(&m, 0, sizeof(m));
   const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
   SSM_CUDA(encode_2d(&m.a_hi, bf, 2, pl->Whi[cur], Q, N, Qp, BK, BM, sw));
   SSM_CUDA(encode_2d(&m.a_lo, bf, 2, pl->Wlo[cur], Q, N, Qp, BK, BM, sw));
   SSM_CUDA(encode_2d(&m.b_hi, bf, 2, pl->Mhi, Q, Q, Qp, BK, BN, sw));
   SSM_CUDA(encode_2d(&m.b_lo, bf, 2, pl->Mlo, Q, Q, Qp, BK, BN, sw));
+  if constexpr (C::fused) {
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const uint64_t ld = (uint64_t)pl->g.ld;
+    SSM_CUDA(encode_2d(&m.ez_c, f32, 4, pl->Z[cur], N, Q, ld, EZW, UG));
+    SSM_CUDA(encode_2d(&m.ez_n, f32, 4, pl->Z[cur], N, Q, ld, ENW, UG));
+    SSM_CUDA(encode_2d(&m.ed, f32, 4, pl->Dl[cur], N, Q, ld, BM, UG));
+    SSM_CUDA(encode_2d(&m.eh, f32, 4, pl->H, N, Q, ld, BM, UG));
+  }
   TcArgs a;
   a.Acc = pl->Acc;
   a.err = pl->dev_err;
@@ -553,7 +738,7 @@ ssm_status launch_gemm(const ssm_plan_s* pl, int cur, double* partial, cudaStrea
   a.xi = (float)pl->xi;
   a.lam_s = (float)pl->lam_s;
   a.inv_xb = (float)(1.0 / (pl->xi + pl->p.beta));
-  tc_gemm_kernel<BN, EPI, NRT><<<gemm_grid(pl, BN), NTHR, Tile<BN>::SMEM_BYTES, s>>>(m, a);
+  tc_gemm_kernel<BN, EPI, NRT><<<gemm_grid(pl, BN), NTHR, C::SMEM_BYTES, s>>>(m, a);
   SSM_LAUNCHED();
   return SSM_OK;
 }
@@ -561,17 +746,40 @@ ssm_status launch_gemm(const ssm_plan_s* pl, int cur, double* partial, cudaStrea
 // staged neighbour rows of the plan's grid: 4 on 3D grids, else at most 2
 int fused_nrt(const ssm_plan_s* pl) { return pl->g.ny > 1 && pl->g.nz > 1 && pl->g.zlink ? 4 : 2; }
 
+template <int BN, int EPI, int NRT>
+ssm_status launch_if_valid(const ssm_plan_s* pl, int cur, double* partial, cudaStream_t s) {
+  if constexpr (Cfg<BN, EPI, NRT>::valid) {
+    return launch_gemm<BN, EPI, NRT>(pl, cur, partial, s);
+  } else {
+    set_error("tensor-core GEMM: tile width too wide for the fused epilogue's shared memory");
+    return SSM_EUNSUPPORTED;
+  }
+}
+
 template <int EPI, int NRT>
 ssm_status gemm_dispatch_n(const ssm_plan_s* pl, int bn, int cur, double* partial, cudaStream_t s) {
   switch (bn) {
-    case 256: return launch_gemm<256, EPI, NRT>(pl, cur, partial, s);
-    case 224: return launch_gemm<224, EPI, NRT>(pl, cur, partial, s);
-    case 192: return launch_gemm<192, EPI, NRT>(pl, cur, partial, s);
-    case 160: return launch_gemm<160, EPI, NRT>(pl, cur, partial, s);
-    case 128: return launch_gemm<128, EPI, NRT>(pl, cur, partial, s);
+    case 256: return launch_if_valid<256, EPI, NRT>(pl, cur, partial, s);
+    case 224: return launch_if_valid<224, EPI, NRT>(pl, cur, partial, s);
+    case 192: return launch_if_valid<192, EPI, NRT>(pl, cur, partial, s);
+    case 160: return launch_if_valid<160, EPI, NRT>(pl, cur, partial, s);
+    case 128: return launch_if_valid<128, EPI, NRT>(pl, cur, partial, s);
     default:
       set_error("tensor-core GEMM: unsupported tile width");
       return SSM_EUNSUPPORTED;
+  }
+}
+
+// whether a tile width has a fused configuration on this plan's grid
+bool fused_width_ok(const ssm_plan_s* pl, int bn) {
+  const bool four = fused_nrt(pl) == 4;
+  switch (bn) {
+    case 256: return four ? Cfg<256, 1, 4>::valid : Cfg<256, 1, 2>::valid;
+    case 224: return four ? Cfg<224, 1, 4>::valid : Cfg<224, 1, 2>::valid;
+    case 192: return four ? Cfg<192, 1, 4>::valid : Cfg<192, 1, 2>::valid;
+    case 160: return four ? Cfg<160, 1, 4>::valid : Cfg<160, 1, 2>::valid;
+    case 128: return four ? Cfg<128, 1, 4>::valid : Cfg<128, 1, 2>::valid;
+    default: return false;
   }
 }
 
@@ -587,25 +795,34 @@ ssm_status gemm_dispatch(const ssm_plan_s* pl, int bn, int cur, cudaStream_t s) 
   return gemm_dispatch<EPI_STORE>(pl, bn, cur, nullptr, s);
 }
 
+template <int BN, int EPI, int NRT>
+cudaError_t set_attr_one() {
+  if constexpr (Cfg<BN, EPI, NRT>::valid) {
+    return cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI, NRT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<BN, EPI, NRT>::SMEM_BYTES);
+  } else {
+    return cudaSuccess;
+  }
+}
+
 template <int BN>
 cudaError_t set_smem_attr() {
-  for (const void* k : {(const void*)tc_gemm_kernel<BN, EPI_STORE, 2>,
-                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE, 2>,
-                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE_CHECK, 2>,
-                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE, 4>,
-                        (const void*)tc_gemm_kernel<BN, EPI_UPDATE_CHECK, 4>}) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::SMEM_BYTES);
+  for (cudaError_t e : {set_attr_one<BN, EPI_STORE, 2>(), set_attr_one<BN, EPI_UPDATE, 2>(),
+                        set_attr_one<BN, EPI_UPDATE_CHECK, 2>(), set_attr_one<BN, EPI_UPDATE, 4>(),
+                        set_attr_one<BN, EPI_UPDATE_CHECK, 4>(), set_attr_one<BN, EPI_REG, 2>(),
+                        set_attr_one<BN, EPI_REG_CHECK, 2>(), set_attr_one<BN, EPI_REG, 4>(),
+                        set_attr_one<BN, EPI_REG_CHECK, 4>()})
     if (e != cudaSuccess) return e;
-  }
   return cudaSuccess;
 }
 
 // choices measured per (device, Q, N, waves, halo rows, fixed tile width), shared by every
 // plan of the process
 struct TcChoice {
-  int bn;
-  bool fused;
+  int bn;        // GEMM width of the two-kernel form and of the register-epilogue kernel
+  int bn_fused;  // width of the staged-epilogue kernel (0: none fits)
+  int form;      // 0: GEMM + update, 1: fused (staged epilogue), 2: fused (register)
 };
 std::mutex g_tune_mutex;
 std::map<std::tuple<int, int, int64_t, int, int, int>, TcChoice> g_tuned;
@@ -627,17 +844,29 @@ ssm_status tune_tile(ssm_plan_s* pl, cudaStream_t s) {
     for (int bn : kTileN)
       if (bn == v) fixed_bn = v;
   }
-  if (const char* env = getenv("SSM_TC_FUSED")) fixed_fused = atoi(env) != 0 ? 1 : 0;
+  if (const char* env = getenv("SSM_TC_FUSED")) {   // 0, 1 (staged) or 2 (register)
+    const int v = atoi(env);
+    fixed_fused = v >= 0 && v <= 2 ? v : 0;
+  }
   if (fixed_bn != 0 && fixed_fused >= 0) {
-    pl->tc_bn = fixed_bn;
+    if (fixed_fused == 1 && !fused_width_ok(pl, fixed_bn)) {
+      set_error("SSM_TC_BN: no fused configuration at this tile width for this grid");
+      return SSM_EUNSUPPORTED;
+    }
+    pl->tc_bn = pl->tc_bn_fused = fixed_bn;
     pl->tc_fused = fixed_fused != 0;
+    pl->tc_fused_reg = fixed_fused == 2;
     return SSM_OK;
   }
   const int nr = (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 && pl->g.zlink ? 2 : 0);
   const auto key = std::make_tuple(pl->device, pl->Q, pl->g.N, pl->waves, nr, fixed_bn);
   auto apply = [&](const TcChoice& c) {
     pl->tc_bn = c.bn;
-    pl->tc_fused = fixed_fused >= 0 ? fixed_fused != 0 : c.fused;
+    pl->tc_bn_fused = c.bn_fused;
+    int form = fixed_fused >= 0 ? fixed_fused : c.form;
+    if (form == 1 && c.bn_fused == 0) form = 2;   // no staged configuration fits
+    pl->tc_fused = form != 0;
+    pl->tc_fused_reg = form == 2;
   };
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -660,7 +889,7 @@ ssm_status tune_tile(ssm_plan_s* pl, cudaStream_t s) {
     SSM_CUDA(cudaEventElapsedTime(ms, e0, e1));
     return SSM_OK;
   };
-  TcChoice c{fixed_bn != 0 ? fixed_bn : 256, false};
+  TcChoice c{fixed_bn != 0 ? fixed_bn : 256, 0, 0};
   ssm_status st = SSM_OK;
   if (fixed_bn == 0) {
     float best_ms = 0.f;
@@ -686,9 +915,30 @@ ssm_status tune_tile(ssm_plan_s* pl, cudaStream_t s) {
           return tc_update(pl, 0, false, nullptr, &parts, s);
         },
         &two_ms);
+    // the fused kernel at every width whose configuration fits (its operand ring is
+    // shallower, so its best width can differ from the GEMM's)
+    for (int bn : kTileN) {
+      if (st != SSM_OK) break;
+      if (fixed_bn != 0 && bn != fixed_bn) continue;
+      if (!fused_width_ok(pl, bn)) continue;
+      float ms = 0.f;
+      st = timed([&] { return gemm_dispatch<EPI_UPDATE>(pl, bn, 0, nullptr, s); }, &ms);
+      if (st == SSM_OK && (c.bn_fused == 0 || ms < fused_ms)) {
+        c.bn_fused = bn;
+        fused_ms = ms;
+      }
+    }
+    // the register-epilogue kernel at the GEMM's width (it needs no shared memory)
+    float reg_ms = 0.f;
     if (st == SSM_OK)
-      st = timed([&] { return gemm_dispatch<EPI_UPDATE>(pl, c.bn, 0, nullptr, s); }, &fused_ms);
-    c.fused = fused_ms < two_ms;
+      st = timed([&] { return gemm_dispatch<EPI_REG>(pl, c.bn, 0, nullptr, s); }, &reg_ms);
+    c.form = 0;
+    float best = two_ms;
+    if (c.bn_fused != 0 && fused_ms < best) {
+      c.form = 1;
+      best = fused_ms;
+    }
+    if (reg_ms < best) c.form = 2;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -726,7 +976,11 @@ ssm_status tc_gemm(ssm_plan_s* pl, int cur, cudaStream_t s) {
   return gemm_dispatch(pl, pl->tc_bn, cur, s);
 }
 
-int tc_gemm_grid(const ssm_plan_s* pl) { return gemm_grid(pl, pl->tc_bn); }
+int tc_tile_width(const ssm_plan_s* pl) {
+  return pl->tc_fused && !pl->tc_fused_reg ? pl->tc_bn_fused : pl->tc_bn;
+}
+
+int tc_gemm_grid(const ssm_plan_s* pl) { return gemm_grid(pl, tc_tile_width(pl)); }
 
 ssm_status tc_iteration(ssm_plan_s* pl, int cur, bool check, double* partial, int* nparts,
                         cudaStream_t s) {
@@ -734,9 +988,14 @@ ssm_status tc_iteration(ssm_plan_s* pl, int cur, bool check, double* partial, in
     SSM_TRY(tc_gemm(pl, cur, s));
     return tc_update(pl, cur, check, partial, nparts, s);
   }
-  *nparts = gemm_grid(pl, pl->tc_bn);
-  return check ? gemm_dispatch<EPI_UPDATE_CHECK>(pl, pl->tc_bn, cur, partial, s)
-               : gemm_dispatch<EPI_UPDATE>(pl, pl->tc_bn, cur, partial, s);
+  if (pl->tc_fused_reg) {
+    *nparts = gemm_grid(pl, pl->tc_bn);
+    return check ? gemm_dispatch<EPI_REG_CHECK>(pl, pl->tc_bn, cur, partial, s)
+                 : gemm_dispatch<EPI_REG>(pl, pl->tc_bn, cur, partial, s);
+  }
+  *nparts = gemm_grid(pl, pl->tc_bn_fused);
+  return check ? gemm_dispatch<EPI_UPDATE_CHECK>(pl, pl->tc_bn_fused, cur, partial, s)
+               : gemm_dispatch<EPI_UPDATE>(pl, pl->tc_bn_fused, cur, partial, s);
 }
 
 }  // namespace ssm

@@ -135,7 +135,9 @@ def test_gemm_tile_widths_agree(monkeypatch, P, Q, dims, iters):
 # ---------------------------------------------------------------------------
 def solve_form(monkeypatch, fused, K, M, dims, lam, beta, iters, check_every, mask=None,
                batch=None, bn=None):
-    monkeypatch.setenv("SSM_TC_FUSED", "1" if fused else "0")
+    """fused: 0 = GEMM + update kernel, 1 = fused with the staged epilogue, 2 = fused with
+    the register epilogue"""
+    monkeypatch.setenv("SSM_TC_FUSED", str(int(fused)))
     if bn is not None:
         monkeypatch.setenv("SSM_TC_BN", str(bn))
     kw = {} if batch is None else {"batch": batch}
@@ -159,9 +161,10 @@ FUSED_CASES = [
 ]
 
 
+@pytest.mark.parametrize("mode", [1, 2], ids=["staged", "register"])
 @pytest.mark.parametrize("P,Q,dims,extra", FUSED_CASES,
                          ids=["2d", "3d", "1d", "2d_mask", "batched_slices"])
-def test_fused_iteration_matches_two_kernel_form(monkeypatch, P, Q, dims, extra):
+def test_fused_iteration_matches_two_kernel_form(monkeypatch, P, Q, dims, extra, mode):
     K, M, _ = synth.random_problem(P, Q, dims, seed=P + Q, snr=50.0)
     kw = {}
     if extra == "mask":
@@ -170,8 +173,8 @@ def test_fused_iteration_matches_two_kernel_form(monkeypatch, P, Q, dims, extra)
     if extra == "batch":   # slices of dims[:2] stacked along the last axis
         kw["batch"] = dims[2]
         dims = dims[:2]
-    F0, i0 = solve_form(monkeypatch, False, K, M, dims, 0.02, 1.5, 400, 7, **kw)
-    F1, i1 = solve_form(monkeypatch, True, K, M, dims, 0.02, 1.5, 400, 7, **kw)
+    F0, i0 = solve_form(monkeypatch, 0, K, M, dims, 0.02, 1.5, 400, 7, **kw)
+    F1, i1 = solve_form(monkeypatch, mode, K, M, dims, 0.02, 1.5, 400, 7, **kw)
     assert i0["iterations"] == i1["iterations"]
     # the residual norms sum the same values in another order (other work split)
     assert i1["res_primal"] == pytest.approx(i0["res_primal"], rel=1e-6)
@@ -181,10 +184,31 @@ def test_fused_iteration_matches_two_kernel_form(monkeypatch, P, Q, dims, extra)
         assert np.all(F1[:, ~kw["mask"]] == 0.0)
 
 
-@pytest.mark.parametrize("bn", [256, 224, 192, 160, 128])
-def test_fused_iteration_every_tile_width(monkeypatch, bn):
-    K, M, _ = synth.random_problem(64, 1600, (40, 30), seed=5, snr=50.0)
-    F0, i0 = solve_form(monkeypatch, False, K, M, (40, 30), 0.02, 1.5, 12, 4, bn=bn)
-    F1, i1 = solve_form(monkeypatch, True, K, M, (40, 30), 0.02, 1.5, 12, 4, bn=bn)
+# the fused kernel's operand ring is 2 stages next to its epilogue ring: widths up to 224
+# fit on 2D grids, up to 192 on 3D grids
+@pytest.mark.parametrize("bn,dims", [(224, (40, 30)), (192, (40, 30)), (160, (40, 30)),
+                                     (128, (40, 30)), (192, (12, 10, 9)), (160, (12, 10, 9)),
+                                     (128, (12, 10, 9))])
+def test_fused_iteration_every_tile_width(monkeypatch, bn, dims):
+    K, M, _ = synth.random_problem(64, 1600, dims, seed=5, snr=50.0)
+    F0, i0 = solve_form(monkeypatch, 0, K, M, dims, 0.02, 1.5, 12, 4, bn=bn)
+    F1, i1 = solve_form(monkeypatch, 1, K, M, dims, 0.02, 1.5, 12, 4, bn=bn)
     assert np.array_equal(F0, F1)
     assert i1["res_primal"] == pytest.approx(i0["res_primal"], rel=1e-6)
+
+
+@pytest.mark.parametrize("bn,dims", [(256, (40, 30)), (224, (12, 10, 9))])
+def test_fused_width_without_room_is_refused(monkeypatch, bn, dims):
+    K, M, _ = synth.random_problem(16, 300, dims, seed=6)
+    with pytest.raises(ssm.SsmError) as e:
+        solve_form(monkeypatch, 1, K, M, dims, 0.02, 1.5, 4, 0, bn=bn)
+    assert e.value.status == ssm.SSM_EUNSUPPORTED
+
+
+def test_register_epilogue_at_the_widest_tile(monkeypatch):
+    """The register epilogue needs no shared memory, so it runs at width 256 (where the
+    staged one does not fit)."""
+    K, M, _ = synth.random_problem(30, 600, (40, 30), seed=8, snr=50.0)
+    F0, i0 = solve_form(monkeypatch, 0, K, M, (40, 30), 0.02, 1.5, 30, 7, bn=256)
+    F2, i2 = solve_form(monkeypatch, 2, K, M, (40, 30), 0.02, 1.5, 30, 7, bn=256)
+    assert np.array_equal(F0, F2)
