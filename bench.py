@@ -35,6 +35,12 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOAD = "dr2d_slice"
+
+
+def describe(w):
+    if w.name == "dr2d_slice":
+        return "2D diffusion-relaxation slice 128x128"
+    return f"{len(w.dims)}D grid {'x'.join(str(d) for d in w.dims)}"
 ITERS_PER_STEP = 100
 CHECK_EVERY = 10
 TTT_TOL = 3e-4
@@ -54,6 +60,9 @@ def parse_args():
     ap.add_argument("--quick", action="store_true", help="headline form only")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
     ap.add_argument("--no-batching", action="store_true", help="skip the batching run")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="workload of the timed steps (default: the 128x128 slice the metric "
+                         "is quoted on; the others serve profiling)")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-iters", type=int, default=100,
                     help="iterations per served request (a fixed budget)")
@@ -184,13 +193,13 @@ def form_key(form, prec):
     return f"{form}_{prec}"
 
 
-def dominant_kernel(form, prec, Q, N, r, fused=False):
+def dominant_kernel(form, prec, Q, N, r, fused=0):
     """(kernel name, source file, bound, algorithmic amount per launch, unit, traffic key).
 
-    The tensor-core form runs either the fused kernel (the GEMM with the update in its
-    epilogue: the whole iteration) or the GEMM + update pair, whichever the plan's
-    autotuner measured faster; its dominant kernel is the GEMM either way, and its bound
-    the tensor-core product's flops."""
+    The tensor-core form runs one of three forms, whichever the plan's autotuner measured
+    fastest: the GEMM + update pair, or the fused kernel (the GEMM with the update in its
+    epilogue: the whole iteration) with a staged (1) or register (2) epilogue. Its
+    dominant kernel is the GEMM either way, and its bound the tensor-core flops."""
     if form == "lowrank":
         # read z and write z' per state element (d cancels from the iteration, see
         # ssm_lowrank.cu); read S, u and write u' per voxel
@@ -200,8 +209,9 @@ def dominant_kernel(form, prec, Q, N, r, fused=False):
         # (for Algorithm 1 the profiled time is the whole iteration, of which the x-step
         # product is this amount of work)
         return ("sgemm_kernel", "ssm_dense.cu", "alu", 2.0 * Q * Q * N, "TFLOP/s", "sgemm_kernel")
-    return ("tc_gemm_kernel", "ssm_tc.cu", "tensor", 3 * 2.0 * Q * Q * N, "TFLOP/s",
-            "tc_gemm_kernel (fused update epilogue)" if fused else "tc_gemm_kernel")
+    key = {0: "tc_gemm_kernel", 1: "tc_gemm_kernel (fused, staged epilogue)",
+           2: "tc_gemm_kernel (fused, register epilogue)"}[fused]
+    return ("tc_gemm_kernel", "ssm_tc.cu", "tensor", 3 * 2.0 * Q * Q * N, "TFLOP/s", key)
 
 
 # --------------------------------------------------------------------------------------
@@ -318,7 +328,7 @@ def bench_ours(args):
                                           "||z-f|| and ||dz|| relative to ||z||")}
         results[key] = rec
         if (form, prec) == head:
-            fused = bool(rec.get("launch", {}).get("tc_fused", 0))
+            fused = int(rec.get("launch", {}).get("tc_fused", 0))
             kname, kfile, bound, amount, unit, tkey = dominant_kernel(form, prec, Q, N,
                                                                       info["rank"], fused)
             avg_s = kms / max(kl, 1) / 1e3
@@ -383,12 +393,13 @@ def bench_ours(args):
             "ms_per_step": hl["rec"]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if head[1] == "fp32" else "bf16x3+f32",
             "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: 2D diffusion-relaxation slice 128x128 "
+            "config": {"workload": f"{WORKLOAD}: {describe(w)} "
                                    f"(N={N}), P={P}, Q={Q}, lambda={w.lam}, beta={w.beta:.4g}",
                        "form": form_key(*head), "iters_per_step": ITERS_PER_STEP,
                        "check_every": CHECK_EVERY, "rank": hl["rec"]["rank"],
                        "plan_ms": hl["plan_ms"],
-                       "l2": "inputs larger than L2 (each Q x N state array is 164 MB)",
+                       "l2": f"inputs larger than L2 (each Q x N state array is "
+                             f"{Q * N * 4 / 1e6:.0f} MB)",
                        "parallelism": f"replicas x{dist.world}"},
             "clocks": hl["clocks"], "e2e": hl["e2e"], "gpu_launches": hl["launches"],
             "roofline": hl["roofline"], "cpu_baseline": cpu and cpu["baseline"],
@@ -629,7 +640,7 @@ def bench_reference(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: 2D diffusion-relaxation slice 128x128 "
+        "config": {"workload": f"{WORKLOAD}: {describe(w)} "
                                f"(N={w.N}), P={w.P}, Q={w.Q}, lambda={w.lam}",
                    "form": "lowrank (Algorithm 2) FP64 oracle"},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": os.cpu_count(),
@@ -646,7 +657,9 @@ def bench_reference(args):
 
 
 def main():
+    global WORKLOAD
     args = parse_args()
+    WORKLOAD = args.workload
     if args.impl == "reference":
         bench_reference(args)
     else:
