@@ -140,14 +140,15 @@ def measured_peaks():
 
 def traffic_record(kernel_file, kernel_name):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is
-    unchanged since the capture (profiles/traffic.json records its hash)."""
+    unchanged since the capture (profiles/traffic.json records its hash) and the capture
+    was of the workload being run."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel_name]
     except (OSError, ValueError, KeyError):
         return None
     src = os.path.join(ROOT, "paper_2401_12890_gb300", "csrc", kernel_file)
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha") != h:
+    if rec.get("source_sha") != h or rec.get("bench_workload", "dr2d_slice") != WORKLOAD:
         return None
     return rec.get("dram_bytes_per_launch_full")
 
