@@ -7,13 +7,17 @@
 //       z' = max(0, (xi z - lambda s (deg z - sum_nbr z) + beta f + d) / (xi + beta))  (Eq. 31)
 //       d' = d - beta (z' - f)                                                      (step 11)
 //       w' = beta z' - d'   -> stored as the BF16 pair (hi, lo) for the next product
-// One kernel does all of it: the epilogue warps apply the element-wise steps to each
-// accumulator tile straight out of TMEM while the MMA warp computes the next tile, so
-// the update's HBM traffic runs under the tensor-core time and M w never goes to
-// memory. (The same GEMM with a plain store epilogue, acc -> memory, followed by the
-// separate TMA-staged update kernel of ssm_tc_update.cu, is kept as the two-kernel
-// form: the tile-width autotuner times that GEMM, and it is the reference the fused
-// kernel is tested against bit for bit.)
+// Three forms of the iteration, chosen per problem shape by a plan-time autotuner:
+//   - GEMM + update: the GEMM's epilogue stores acc to memory, and the TMA-staged update
+//     kernel of ssm_tc_update.cu applies the element-wise steps;
+//   - fused, staged epilogue: the epilogue warps apply the steps to each accumulator tile
+//     straight out of TMEM, reading z, its neighbour rows, d and h from a shared-memory
+//     ring that a producer warp fills by TMA (fits up to width 224, 192 on 3D grids);
+//   - fused, register epilogue: the same, with the reads software-pipelined in
+//     registers (any width).
+// In the fused forms M w never goes to memory, and the element-wise work runs while the
+// MMA warp computes the next tile. All three apply the same steps (DenseStep) to the same
+// accumulator values and give the same bits.
 //
 // Precision ("BF16x3"): w and M are each split into BF16 hi + lo parts
 // (x_hi = bf16(x), x_lo = bf16(x - x_hi)), and M w is accumulated in FP32 in tensor
@@ -31,9 +35,10 @@
 // voxel-tile major so concurrently running CTAs share w tiles in L2. Warp 0 issues TMA
 // loads into a smem ring; one thread of warp 1 issues the tcgen05.mma chain (3 MMAs
 // per K = 16 step) and commits stage releases and accumulator completions to
-// mbarriers; warps 2-5 drain the accumulator (tcgen05.ld) to global memory. Two
-// accumulators (TMEM columns 0 and 256) alternate so draining one tile overlaps the
-// next tile's MMAs. Every mbarrier wait is bounded.
+// mbarriers; warps 2-9 drain the accumulator (tcgen05.ld), two per TMEM lane quarter;
+// warp 10 feeds the staged epilogue's ring. Two accumulators (TMEM columns 0 and 256)
+// alternate so draining one tile overlaps the next tile's MMAs. Every mbarrier wait is
+// bounded.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -149,8 +154,12 @@ struct Cfg {
   static constexpr bool fused = epi_staged(EPI);   // an epilogue ring in shared memory
   static constexpr int NS = fused ? 2 : Tile<BN>::NS;
   static constexpr int RESERVE = 1024 + 256;    // alignment slack, barriers, TMEM slot
+  // static shared memory of the residual-test variants: the reduction array, which the
+  // compiler pads to 1024 bytes to keep the 1024-aligned dynamic window aligned; the
+  // per-block limit counts it with the dynamic bytes
+  static constexpr int STATIC_MAX = 1024;
   static constexpr int EST = EpiStage<NRT>::bytes;
-  static constexpr int room = kSmemLimit - RESERVE - NS * Tile<BN>::STAGE_BYTES;
+  static constexpr int room = kSmemLimit - RESERVE - STATIC_MAX - NS * Tile<BN>::STAGE_BYTES;
   // an even number of stages: slot = sequence index mod NBE then has the parity of the
   // sequence index, so every slot is consumed by one half of the epilogue warps and its
   // barrier phases complete in that half's order (with an odd count the halves would
