@@ -135,13 +135,15 @@ constexpr int ENW = BM + 4;   // staged neighbour row: 4-aligned base .. +BM+3
 // One stage of the fused epilogue's ring: a group of UG compartments of a voxel tile --
 // z with its x halo, NRT neighbour rows (the -+nx, -+nx*ny rows), d and h -- each a TMA
 // box (128-byte-aligned offsets).
-template <int NRT>
+// DH = false leaves d and h out of the stage (the epilogue warps then prefetch them into
+// registers one group ahead), for the configurations whose ring would not fit otherwise.
+template <int NRT, bool DH = true>
 struct EpiStage {
   static constexpr int zc = 0;
   static constexpr int zn = UG * EZW * 4;
   static constexpr int dd = zn + NRT * UG * ENW * 4;
   static constexpr int hh = dd + UG * BM * 4;
-  static constexpr int bytes = hh + UG * BM * 4;
+  static constexpr int bytes = DH ? hh + UG * BM * 4 : dd;
   static_assert(zn % 128 == 0 && dd % 128 == 0 && hh % 128 == 0 && bytes % 128 == 0, "layout");
 };
 
@@ -158,13 +160,16 @@ struct Cfg {
   // compiler pads to 1024 bytes to keep the 1024-aligned dynamic window aligned; the
   // per-block limit counts it with the dynamic bytes
   static constexpr int STATIC_MAX = 1024;
-  static constexpr int EST = EpiStage<NRT>::bytes;
   static constexpr int room = kSmemLimit - RESERVE - STATIC_MAX - NS * Tile<BN>::STAGE_BYTES;
   // an even number of stages: slot = sequence index mod NBE then has the parity of the
   // sequence index, so every slot is consumed by one half of the epilogue warps and its
   // barrier phases complete in that half's order (with an odd count the halves would
   // alternate on a slot, and a half waiting by parity could pass on an older phase)
-  static constexpr int NBE = fused ? ((room / EST > 4 ? 4 : room / EST) & ~1) : 0;
+  static constexpr int even_stages(int est) { return (room / est > 4 ? 4 : room / est) & ~1; }
+  // d and h are staged unless that leaves fewer than two stages
+  static constexpr bool DH = even_stages(EpiStage<NRT, true>::bytes) >= 2;
+  static constexpr int EST = EpiStage<NRT, DH>::bytes;
+  static constexpr int NBE = fused ? even_stages(EST) : 0;
   static constexpr bool valid = !fused || NBE >= 2;
   static constexpr int SMEM_BYTES = NS * Tile<BN>::STAGE_BYTES + NBE * EST + RESERVE;
 };
@@ -257,7 +262,7 @@ template <int BN, int EPI, int NRT>
 __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant__ TcMaps maps,
                                                           const TcArgs a) {
   using C = Cfg<BN, EPI, NRT>;
-  using ES = EpiStage<NRT>;
+  using ES = EpiStage<NRT, C::DH>;
   constexpr int NS = C::NS, NBE = C::NBE, STAGE_BYTES = Tile<BN>::STAGE_BYTES;
   constexpr int B_BYTES = Tile<BN>::B_BYTES;
   constexpr uint32_t IDESC = Tile<BN>::IDESC;
@@ -342,7 +347,8 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
         const int64_t plane = (int64_t)nx * ny;
         const int64_t off[4] = {ny > 1 ? -(int64_t)nx : -plane, ny > 1 ? (int64_t)nx : plane,
                                 -plane, plane};
-        const unsigned bytes = (unsigned)((UG * EZW + NR * UG * ENW + 2 * UG * BM) * 4);
+        const unsigned bytes =
+            (unsigned)((UG * EZW + NR * UG * ENW + (C::DH ? 2 * UG * BM : 0)) * 4);
         tma_prefetch_map(&maps.ez_c);
         tma_prefetch_map(&maps.ez_n);
         int i = 0;
@@ -363,8 +369,10 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
             for (int j = 0; j < NR; ++j)
               tma_load_2d(st + ES::zn + j * UG * ENW * 4, &maps.ez_n,
                           (int)floor4i(n0 + off[j]), q0, &efull[slot]);
-            tma_load_2d(st + ES::dd, &maps.ed, (int)n0, q0, &efull[slot]);
-            tma_load_2d(st + ES::hh, &maps.eh, (int)n0, q0, &efull[slot]);
+            if constexpr (C::DH) {
+              tma_load_2d(st + ES::dd, &maps.ed, (int)n0, q0, &efull[slot]);
+              tma_load_2d(st + ES::hh, &maps.eh, (int)n0, q0, &efull[slot]);
+            }
           }
         }
       }
@@ -418,6 +426,38 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
     // pair first when there is a y axis)
     const int64_t off[4] = {ny > 1 ? -(int64_t)nx : -plane, ny > 1 ? (int64_t)nx : plane,
                             -plane, plane};
+    // staged epilogue whose stages leave d and h out: those of this warp's next group are
+    // prefetched into registers one group ahead; (pt, pcg) walks the CTA's (tile, group)
+    // sequence in the order the epilogue producer stages it, two positions per group of
+    // this half
+    float dnext[UG], hnext[UG];
+    int pt = blockIdx.x, pcg = 0;
+    auto ngroups = [&](int tt) {
+      const int rest = a.Q - (tt % a.ntq) * BN;
+      return min(BN / UG, (rest + UG - 1) / UG);
+    };
+    auto step_seq = [&]() {
+      if (++pcg >= ngroups(pt)) {
+        pcg = 0;
+        pt += gridDim.x;
+      }
+    };
+    auto load_dh = [&]() {
+      if (pt < ntiles) {
+        const int64_t nn = (int64_t)(pt / a.ntq) * BM + row;   // < ld: a valid address
+        const int q0n = (pt % a.ntq) * BN + pcg * UG;
+#pragma unroll
+        for (int j = 0; j < UG; ++j) {
+          const int64_t o = (int64_t)min(q0n + j, a.Q - 1) * ld + nn;
+          dnext[j] = __ldg(a.Din + o);
+          hnext[j] = __ldg(a.H + o);
+        }
+      }
+    };
+    if constexpr (epi_staged(EPI) && !C::DH) {
+      if (half == 1) step_seq();
+      load_dh();
+    }
     int it = 0;
     int gseq = 0;   // position in the CTA's sequence of (tile, group) (fused epilogue)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
@@ -475,6 +515,17 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
             const float* zn_ = reinterpret_cast<const float*>(st + ES::zn);
             const float* dd_ = reinterpret_cast<const float*>(st + ES::dd);
             const float* hh_ = reinterpret_cast<const float*>(st + ES::hh);
+            float dcur[UG], hcur[UG];
+            if constexpr (!C::DH) {
+#pragma unroll
+              for (int j = 0; j < UG; ++j) {
+                dcur[j] = dnext[j];
+                hcur[j] = hnext[j];
+              }
+              step_seq();
+              step_seq();
+              load_dh();
+            }
             if (!failed) {
   #pragma unroll
               for (int j = 0; j < UG; ++j) {
@@ -486,9 +537,10 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
                 for (int kk = 0; kk < NRT; ++kk)
                   nb += nok[kk] ? zn_[(kk * UG + j) * ENW + row + rem[kk]] : 0.f;
                 const int q = q0 + j;
-                const float f = __fadd_rn(hh_[j * BM + row], v[j]);
+                const float f = __fadd_rn(C::DH ? hh_[j * BM + row] : hcur[j], v[j]);
                 float dn, w;
-                const float zn = step.apply(z, dd_[j * BM + row], f, deg, nb, dn, w);
+                const float zn =
+                    step.apply(z, C::DH ? dd_[j * BM + row] : dcur[j], f, deg, nb, dn, w);
                 if (in && q < a.Q) {
                   const int64_t o = (int64_t)q * ld + n;
                   a.Zout[o] = zn;
