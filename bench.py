@@ -143,7 +143,8 @@ def traffic_record(kernel_file, kernel_name):
     unchanged since the capture (profiles/traffic.json records its hash) and the capture
     was of the workload being run."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel_name]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[
+            f"{kernel_name} @ {WORKLOAD}"]
     except (OSError, ValueError, KeyError):
         return None
     src = os.path.join(ROOT, "paper_2401_12890_gb300", "csrc", kernel_file)
