@@ -51,15 +51,16 @@ def inversion_recovery_dictionary(ti_ms, te_ms, t1_ms, t2_ms):
     return K.reshape(ti.size * te.size, t1.size * t2.size)
 
 
-def spgr_fingerprint_dictionary(n_tp, t1_ms, t2_ms, seed):
+def spgr_fingerprint_dictionary(n_tp, t1_ms, t2_ms, seed, b1=1.0):
     """Spoiled-gradient-echo fingerprinting dictionary, columns L2-normalised.
 
     Flip angles alpha_p ~ U(5, 70) degrees and TR_p ~ U(10, 15) ms are drawn from the
     seed; TE_p = TR_p / 2. Longitudinal magnetisation starts at 1; each time point
     reads Mz sin(alpha) exp(-TE/T2) and then relaxes Mz <- 1 - (1 - Mz cos a) exp(-TR/T1).
+    b1 scales the whole flip-angle train (the transmit field's relative amplitude).
     """
     rng = np.random.default_rng(seed)
-    alpha = np.deg2rad(rng.uniform(5.0, 70.0, n_tp))
+    alpha = np.deg2rad(rng.uniform(5.0, 70.0, n_tp)) * float(b1)
     tr = rng.uniform(10.0, 15.0, n_tp)
     te = 0.5 * tr
     t1 = np.asarray(t1_ms, np.float64)
@@ -266,6 +267,41 @@ def random_problem(P, Q, dims, seed, snr=None, nonneg_k=True, full_rank=False):
     if snr:
         M = M + rng.standard_normal(M.shape) * (np.abs(M).max() / snr)
     return K, M, F
+
+
+def b1_varying_problem(dims, levels, n_tp=60, t1_ms=None, t2_ms=None, seed=0, snr=100.0,
+                       b1_range=(0.8, 1.2)):
+    """A fingerprinting problem with a spatially varying dictionary (one per B1 level).
+
+    A smooth B1 field over the grid is quantised to `levels` values spread evenly over
+    `b1_range`; voxel n is labelled with its level c(n) and its data is
+    m_n = K_{c(n)} f_n + noise, K_c the dictionary at that B1 (the same seeded flip-angle
+    and TR train, scaled). The ground truth has two smooth nonnegative spectral peaks.
+    Returns (Ks, labels, M, F_true), float64.
+    """
+    rng = np.random.default_rng(seed)
+    t1 = np.geomspace(300.0, 3000.0, 6) if t1_ms is None else np.asarray(t1_ms, np.float64)
+    t2 = np.geomspace(20.0, 300.0, 5) if t2_ms is None else np.asarray(t2_ms, np.float64)
+    b1_levels = np.linspace(b1_range[0], b1_range[1], int(levels))
+    Ks = [spgr_fingerprint_dictionary(n_tp, t1, t2, seed + 1, b1=b) for b in b1_levels]
+    field = _smooth_field(rng, dims)
+    lo, hi = field.min(), field.max()
+    u = (field - lo) / max(hi - lo, 1e-300)
+    labels = np.minimum((u * levels).astype(np.int64), levels - 1)
+    Q = t1.size * t2.size
+    N = int(np.prod(dims))
+    a1 = 0.5 + 0.5 * _smooth_field(rng, dims)
+    a2 = np.clip(0.5 + 0.5 * _smooth_field(rng, dims), 0.0, None)
+    F = np.zeros((Q, N))
+    F[rng.integers(0, Q)] = a1
+    F[rng.integers(0, Q)] += a2
+    M = np.empty((n_tp, N))
+    for c, K in enumerate(Ks):
+        sel = labels == c
+        M[:, sel] = K @ F[:, sel]
+    if snr:
+        M = M + rng.standard_normal(M.shape) * (np.abs(M).max() / snr)
+    return Ks, labels, M, F
 
 
 def grid_dims_for_n(n: int):
