@@ -66,8 +66,13 @@ typedef enum {
 
 typedef enum {
   SSM_FP32 = 0,            /* FP32 arithmetic, FP32 state                           */
-  SSM_BF16X3 = 1           /* dense form: BF16 hi/lo split products (3 tcgen05 MMAs
+  SSM_BF16X3 = 1,          /* dense form: BF16 hi/lo split products (3 tcgen05 MMAs
                               per tile, FP32 accumulation), FP32 state              */
+  SSM_TF32X3 = 2           /* low-rank form: both rank-r products of an iteration
+                              (V a and V^T w, Eq. 28) on the tcgen05 tensor cores,
+                              kind::tf32 with TF32 hi/lo split operands (3 MMAs per K
+                              step), FP32 accumulation; z and u FP32. The rank is
+                              padded to 32 or 64 (r <= 64; r <= 32 on 3D grids)     */
 } ssm_precision;
 
 typedef struct {
@@ -82,7 +87,8 @@ typedef struct {
   int rank;                /* low-rank form: 0 = smallest r with
                               ||K - K_r||_F < rank_tol ||K||_F (Sec. III-E), > 0 = r */
   double rank_tol;         /* <= 0 selects 5e-5 (the paper's 0.005 %)               */
-  int precision;           /* ssm_precision (dense form; low-rank runs FP32)        */
+  int precision;           /* ssm_precision: dense form FP32 or BF16X3; low-rank form
+                              FP32 or TF32X3 (BF16X3 there runs FP32); ADMM FP32     */
   int stencil_pairs;       /* 2 = literal Eq. 8 (each neighbour pair counted from
                               both ends, D^T D = 2 L); 1 = once per pair (D^T D = L) */
   int max_iter;            /* iteration budget (>= 0)                               */
@@ -103,6 +109,22 @@ typedef struct {
   double res_primal;       /* ||z - f|| / ||z|| at the last test (-1: none)          */
   double res_change;       /* ||z^{k+1} - z^k|| / ||z^{k+1}|| at the last test      */
   double plan_ms;          /* device time of ssm_plan                               */
+  /* The largest eigenvalue of the Hessian of Eq. 7, H = I (x) K^T K + lambda D^T D (x) I,
+   * which bounds the step of a gradient method on Eq. 7; xi_p of Eq. 32 is to exceed
+   * 0.75 lambda ||D^T D|| (the convergence condition the paper cites, Sec. III-C). H is
+   * a Kronecker sum, so lambda_max(H) = lambda_max(K^T K) + lambda lambda_max(D^T D),
+   * and D^T D on the box grid is a Kronecker sum of path-graph Laplacians; ssm_plan runs
+   * one FP64 power iteration on the device per factor (K^T K via the Gram matrix of the
+   * smaller side; one per grid axis of 2 .. 8192 voxels). With a mask the grid values
+   * are the box grid's (an upper bound of the masked operator's).                     */
+  double hess_norm;        /* lambda_max(K^T K) + lambda lambda_max(D^T D)           */
+  double kk_norm;          /* lambda_max(K^T K) by power iteration (sigma_1^2)       */
+  double dtd_norm_power;   /* lambda_max(D^T D) by power iteration                   */
+  int power_iters;         /* most steps any of the power iterations took            */
+  int power_converged;     /* 1: every power iteration met its stopping rule (an
+                              increase of at most 1e-15 relative over 32 steps); 0:
+                              one hit its cap (its value is a lower bound) or an axis
+                              longer than 8192 voxels was left out                  */
 } ssm_info;
 
 /* Fill `p` with defaults: 2D, lambda 0, beta 1, xi_p rule, low-rank auto rank,
@@ -206,6 +228,13 @@ ssm_status ssm_objective_noalloc(const float* K_dev, int P, int Q, const float* 
                                  int64_t ldm, const float* F_dev, int64_t ldf, int ndim,
                                  const int64_t* dims, double lambda, int stencil_pairs,
                                  double* J_host, void* stream);
+
+/*
+ * The plan-level fields of ssm_info (rank, gram_side, xi_p, dtd_norm, sigma1, plan_ms and
+ * the power-iteration results) without solving; status SSM_OK, iterations 0, residuals
+ * -1. Host only (no device work).
+ */
+ssm_status ssm_plan_info(ssm_plan_t plan, ssm_info* info);
 
 /*
  * Read back the plan's factors (for tests): sigma (min(P,Q) doubles, descending) and,

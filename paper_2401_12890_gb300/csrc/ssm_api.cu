@@ -82,6 +82,12 @@ double dtd_norm_closed(const int64_t* dims, int ndim, int pairs) {
   return s * t;
 }
 
+// floats of one partial-u buffer of the low-rank forms
+int64_t lowrank_state_floats(const ssm_plan_s* pl, int64_t grid) {
+  return pl->p.precision == SSM_TF32X3 ? lrtc_partial_floats(pl, grid)
+                                       : lowrank_partial_floats(pl, grid);
+}
+
 int padded_rank(int r) {
   static const int opts[] = {4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64};
   for (int o : opts)
@@ -148,7 +154,7 @@ ssm_status validate(const ssm_params* p) {
     set_error("unknown form");
     return SSM_EINVAL;
   }
-  if (p->precision != SSM_FP32 && p->precision != SSM_BF16X3) {
+  if (p->precision != SSM_FP32 && p->precision != SSM_BF16X3 && p->precision != SSM_TF32X3) {
     set_error("unknown precision");
     return SSM_EINVAL;
   }
@@ -174,6 +180,10 @@ void release(ssm_plan_s* pl) {
   dfree(pl->K32);
   dfree(pl->Kr32);
   dfree(pl->V32);
+  dfree(pl->V1h);
+  dfree(pl->V1l);
+  dfree(pl->V2h);
+  dfree(pl->V2l);
   dfree(pl->coefA);
   dfree(pl->coefW);
   dfree(pl->Mq32);
@@ -242,8 +252,17 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   SSM_TRY(dalloc(&E, (size_t)n * n, s));
   SSM_TRY(dalloc(&scratch, (size_t)n * n + 2, s));
   SSM_TRY(gram_fp64(pl->K64, P, Q, pl->gram_side, A, s));
+  // lambda_max of the Hessian of Eq. 7 by FP64 power iteration (reads A before Jacobi
+  // overwrites it)
+  ssm_status st = hessian_power(pl, A, n, s);
+  if (st != SSM_OK) {
+    cudaFreeAsync(A, s);
+    cudaFreeAsync(E, s);
+    cudaFreeAsync(scratch, s);
+    return st;
+  }
   std::vector<double> evals;
-  ssm_status st = jacobi_eigen(A, n, E, scratch, evals, s);
+  st = jacobi_eigen(A, n, E, scratch, evals, s);
   if (st != SSM_OK) {
     cudaFreeAsync(A, s);
     cudaFreeAsync(E, s);
@@ -285,6 +304,18 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
       set_error("low-rank form supports r <= 64; use the dense form for higher ranks");
       return SSM_EUNSUPPORTED;
     }
+    if (p.precision == SSM_TF32X3) {
+      // the tensor-core form pads the rank to its MMA shapes (32 or 64; the padding
+      // ranks carry zero weights, basis vectors and projections)
+      pl->R = lrtc_padded_rank(pl->r, pl->g.nz > 1 && pl->g.zlink);
+      if (pl->R == 0) {
+        cudaFreeAsync(A, s);
+        cudaFreeAsync(E, s);
+        cudaFreeAsync(scratch, s);
+        set_error("the TF32x3 low-rank form supports r <= 64 (r <= 32 on 3D grids)");
+        return SSM_EUNSUPPORTED;
+      }
+    }
   } else {
     pl->r = n;
     pl->R = 0;
@@ -294,6 +325,13 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
     cudaFreeAsync(E, s);
     cudaFreeAsync(scratch, s);
     set_error("the ADMM form runs in FP32 only");
+    return SSM_EUNSUPPORTED;
+  }
+  if (p.form == SSM_FORM_DENSE && p.precision == SSM_TF32X3) {
+    cudaFreeAsync(A, s);
+    cudaFreeAsync(E, s);
+    cudaFreeAsync(scratch, s);
+    set_error("TF32x3 is a precision of the low-rank form (the dense form offers BF16x3)");
     return SSM_EUNSUPPORTED;
   }
   pl->Qp = (int)round_up(Q, 64);
@@ -308,6 +346,13 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
     SSM_TRY(palloc(pl, &pl->V32, (size_t)Q * pl->R, s));
     SSM_TRY(palloc(pl, &pl->coefA, (size_t)pl->R, s));
     SSM_TRY(palloc(pl, &pl->coefW, (size_t)pl->R, s));
+    if (p.precision == SSM_TF32X3) {
+      pl->lrtc_qs = (int)round_up(Q, 32);
+      SSM_TRY(palloc(pl, &pl->V1h, (size_t)Q * pl->R, s));
+      SSM_TRY(palloc(pl, &pl->V1l, (size_t)Q * pl->R, s));
+      SSM_TRY(palloc(pl, &pl->V2h, (size_t)pl->R * pl->lrtc_qs, s));
+      SSM_TRY(palloc(pl, &pl->V2l, (size_t)pl->R * pl->lrtc_qs, s));
+    }
   } else {
     SSM_TRY(palloc(pl, &pl->Gq32, (size_t)Q * n, s));
     SSM_TRY(palloc(pl, &pl->Mq32, (size_t)Q * pl->Qp, s));
@@ -354,10 +399,16 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
     maxparts = std::max(admm_partial_rows(pl), dense_max_partials(pl));
   } else if (p.form == SSM_FORM_LOWRANK) {
     SSM_TRY(palloc(pl, &pl->S, (size_t)pl->R * pl->g.ld, s));
-    pl->lr_grid = lowrank_grid(pl);
-    const size_t pf = (size_t)lowrank_partial_floats(pl, pl->lr_grid);
+    if (p.precision == SSM_TF32X3) {
+      SSM_TRY(lrtc_prepare());
+      pl->lr_grid = lrtc_grid(pl);
+      maxparts = (int)pl->lr_grid;
+    } else {
+      pl->lr_grid = lowrank_grid(pl);
+      maxparts = lowrank_max_partials(pl);
+    }
+    const size_t pf = (size_t)lowrank_state_floats(pl, pl->lr_grid);
     for (int i = 0; i < 2; ++i) SSM_TRY(palloc(pl, &pl->U[i], pf, s));
-    maxparts = lowrank_max_partials(pl);
   } else {
     SSM_TRY(palloc(pl, &pl->C32, (size_t)n * pl->g.ld, s));
     SSM_TRY(palloc(pl, &pl->H, QN, s));
@@ -417,6 +468,16 @@ ssm_status footprint_impl(const ssm_params& p, bool staging, int waves, int64_t*
       set_error("low-rank form supports r <= 64; use the dense form for higher ranks");
       return SSM_EUNSUPPORTED;
     }
+    if (p.precision == SSM_TF32X3) {
+      // without a fixed rank the bound takes the largest padding the grid allows
+      const bool three_d = t.g.nz > 1 && zlink;
+      t.R = lrtc_padded_rank(p.rank > 0 ? t.r : (three_d ? 32 : 64), three_d);
+      if (t.R == 0) {
+        set_error("the TF32x3 low-rank form supports r <= 64 (r <= 32 on 3D grids)");
+        return SSM_EUNSUPPORTED;
+      }
+      t.lrtc_qs = (int)round_up(p.Q, 32);
+    }
   }
   int64_t b = 0;
   auto add = [&](int64_t elem, int64_t count) { b += elem * count; };
@@ -430,6 +491,7 @@ ssm_status footprint_impl(const ssm_params& p, bool staging, int waves, int64_t*
   if (p.form == SSM_FORM_LOWRANK) {
     add(4, Q * t.R);                          // V32
     add(4, 2 * (int64_t)t.R);                 // coefA, coefW
+    if (p.precision == SSM_TF32X3) add(4, 2 * (Q + t.lrtc_qs) * t.R);  // V1h/l, V2h/l
   } else {
     add(4, Q * n);                            // Gq32
     add(4, Q * t.Qp);                         // Mq32
@@ -450,9 +512,14 @@ ssm_status footprint_impl(const ssm_params& p, bool staging, int waves, int64_t*
     maxparts = std::max<int64_t>(admm_partial_rows(&t), dense_max_partials(&t));
   } else if (p.form == SSM_FORM_LOWRANK) {
     add(4, (int64_t)t.R * ld);                // S
-    t.lr_grid = lowrank_grid(&t);
-    add(4, 2 * lowrank_partial_floats(&t, t.lr_grid));  // U[2]
-    maxparts = lowrank_max_partials(&t);
+    if (p.precision == SSM_TF32X3) {
+      t.lr_grid = lrtc_grid(&t);
+      maxparts = t.lr_grid;
+    } else {
+      t.lr_grid = lowrank_grid(&t);
+      maxparts = lowrank_max_partials(&t);
+    }
+    add(4, 2 * lowrank_state_floats(&t, t.lr_grid));  // U[2]
   } else {
     add(4, n * ld);                           // C32
     add(4, QN);                               // H
@@ -553,7 +620,10 @@ ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, bool check_next, i
   }
   SSM_TRY(prof_mark(pl, true, s));
   if (p.form == SSM_FORM_LOWRANK) {
-    SSM_TRY(lowrank_iteration(pl, cur, check, check_next, pl->red, nparts, s));
+    if (p.precision == SSM_TF32X3)
+      SSM_TRY(lrtc_iteration(pl, cur, check, check_next, pl->red, nparts, s));
+    else
+      SSM_TRY(lowrank_iteration(pl, cur, check, check_next, pl->red, nparts, s));
     return prof_mark(pl, false, s);
   }
   if (p.precision == SSM_FP32) {
@@ -649,6 +719,14 @@ ssm_status run_block_graph(ssm_plan_s* pl, int cur, int k, int L, const IsCheck&
   return SSM_OK;
 }
 
+void fill_power_info(const ssm_plan_s* pl, ssm_info* info) {
+  info->hess_norm = pl->hess_power;
+  info->kk_norm = pl->kk_power;
+  info->dtd_norm_power = pl->dtd_power;
+  info->power_iters = pl->power_iters;
+  info->power_converged = pl->power_conv;
+}
+
 ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int64_t ldf,
                       ssm_info* info, cudaStream_t s) {
   const ssm_params& p = pl->p;
@@ -661,7 +739,7 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
       SSM_CUDA(cudaMemsetAsync(pl->S + (size_t)pl->r * ld, 0,
                                sizeof(float) * (size_t)(pl->R - pl->r) * ld, s));
     SSM_CUDA(cudaMemsetAsync(
-        pl->U[0], 0, sizeof(float) * (size_t)lowrank_partial_floats(pl, pl->lr_grid), s));
+        pl->U[0], 0, sizeof(float) * (size_t)lowrank_state_floats(pl, pl->lr_grid), s));
   } else {
     SSM_TRY(project_data(pl, M, ldm, pl->n, s));
     // h = M g = sum_i Gq_i c_i
@@ -751,6 +829,7 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
     info->res_primal = rp;
     info->res_change = rc;
     info->plan_ms = pl->plan_ms;
+    fill_power_info(pl, info);
   }
   return result;
 }
@@ -943,6 +1022,25 @@ ssm_status ssm_plan_factors(ssm_plan_t plan, double* sigma_host, double* vr_host
         vr_host[(size_t)q * plan->r + i] = v;
       }
   }
+  return SSM_OK;
+}
+
+ssm_status ssm_plan_info(ssm_plan_t plan, ssm_info* info) {
+  if (!plan || !info) {
+    set_error("NULL argument");
+    return SSM_EINVAL;
+  }
+  std::memset(info, 0, sizeof(*info));
+  info->status = SSM_OK;
+  info->rank = plan->r;
+  info->gram_side = plan->gram_side;
+  info->xi_p = plan->xi;
+  info->dtd_norm = plan->dtd_norm;
+  info->sigma1 = plan->sigma1;
+  info->res_primal = -1.0;
+  info->res_change = -1.0;
+  info->plan_ms = plan->plan_ms;
+  fill_power_info(plan, info);
   return SSM_OK;
 }
 

@@ -115,6 +115,9 @@ struct ssm_plan_s {
   int gram_side = 0;           // 0: K K^T, 1: K^T K
   int r = 0, R = 0;            // rank used, padded rank (multiple of 4)
   double xi = 0, dtd_norm = 0, sigma1 = 0, lam_s = 0;
+  // largest eigenvalues by FP64 power iteration (ssm_power.cu): K^T K, D^T D, the Hessian
+  double kk_power = 0, dtd_power = 0, hess_power = 0;
+  int power_iters = 0, power_conv = 0;
   std::vector<double> sigma;   // n singular values, descending
   std::vector<int> perm;       // eigen order (descending) into the Jacobi output
   float plan_ms = 0.f;
@@ -129,6 +132,12 @@ struct ssm_plan_s {
   float* K32 = nullptr;        // P x Q (objective with the full K)
   float* Kr32 = nullptr;       // P x Q (objective with K_r)
   float* V32 = nullptr;        // Q x R  [q][i]  low-rank right singular vectors
+  // TF32x3 low-rank form: V (Q x R) and V^T (R x lrtc_qs), split into TF32 hi/lo parts
+  float* V1h = nullptr;
+  float* V1l = nullptr;
+  float* V2h = nullptr;
+  float* V2l = nullptr;
+  int lrtc_qs = 0;             // row stride of V^T: Q rounded up to 32
   float* coefA = nullptr;      // R      1/(beta + sigma_i^2)
   float* coefW = nullptr;      // R      sigma_i^2/(beta^2 + beta sigma_i^2)
   double* alpha64 = nullptr;   // n      S_i = alpha_i c_i
@@ -203,6 +212,8 @@ ssm_status gram_fp64(const double* K, int P, int Q, int side, double* A, cudaStr
 ssm_status jacobi_eigen(double* A, int n, double* E, double* scratch, std::vector<double>& evals,
                         cudaStream_t s);
 ssm_status factors_fp64(ssm_plan_s* pl, const double* E, cudaStream_t s);
+// power iterations for lambda_max of K^T K (Gram A, n x n) and D^T D (ssm_power.cu)
+ssm_status hessian_power(ssm_plan_s* pl, const double* A, int n, cudaStream_t s);
 ssm_status form_dense_inverse(ssm_plan_s* pl, cudaStream_t s);
 ssm_status beta_weights(ssm_plan_s* pl, cudaStream_t s);
 ssm_status project_data(const ssm_plan_s* pl, const float* M, int64_t ldm, int ncomp,
@@ -218,6 +229,15 @@ ssm_status lowrank_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, 
 int lowrank_max_partials(const ssm_plan_s* pl);
 int64_t lowrank_grid(const ssm_plan_s* pl);
 int64_t lowrank_partial_floats(const ssm_plan_s* pl, int64_t grid);
+
+// low-rank iteration with both rank-r products on the tensor cores (ssm_lowrank_tc.cu)
+int lrtc_padded_rank(int r, bool three_d);
+int64_t lrtc_grid(const ssm_plan_s* pl);
+int64_t lrtc_partial_floats(const ssm_plan_s* pl, int64_t grid);
+ssm_status lrtc_prepare();
+ssm_status lrtc_split_basis(ssm_plan_s* pl, cudaStream_t s);
+ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, double* partial,
+                          int* nparts, cudaStream_t s);
 
 // dense iteration and shared kernels (ssm_dense.cu)
 ssm_status sgemm(int M, int N, int K, float alpha, const float* A, int64_t lda,

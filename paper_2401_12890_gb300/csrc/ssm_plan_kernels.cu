@@ -447,6 +447,7 @@ ssm_status beta_weights(ssm_plan_s* pl, cudaStream_t s) {
         pl->Kt64, Q, n, pl->sig64, pl->r, pl->R, pl->gram_side, pl->p.beta, pl->V32, pl->coefA,
         pl->coefW, floor);
     SSM_LAUNCHED();
+    if (pl->V1h) SSM_TRY(lrtc_split_basis(pl, s));
   } else {
     gq_kernel<<<nblk((int64_t)Q * n, 256), 256, 0, s>>>(pl->Kt64, Q, n, pl->sig64, pl->p.beta,
                                                         pl->Gq32);

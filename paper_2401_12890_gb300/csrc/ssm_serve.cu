@@ -53,8 +53,12 @@ bool same_plan(const ssm_params& a, const ssm_params& b) {
     if (a.dims[d] != b.dims[d]) return false;
   const double xa = a.xi_p > 0 ? a.xi_p : 0.0, xb = b.xi_p > 0 ? b.xi_p : 0.0;
   const double ta = a.rank_tol > 0 ? a.rank_tol : 5e-5, tb = b.rank_tol > 0 ? b.rank_tol : 5e-5;
-  const int pa = a.form != SSM_FORM_LOWRANK ? a.precision : 0;
-  const int pb = b.form != SSM_FORM_LOWRANK ? b.precision : 0;
+  // the low-rank form runs FP32 unless TF32X3 is asked for (BF16X3 there is FP32)
+  auto norm_prec = [](const ssm_params& x) {
+    if (x.form != SSM_FORM_LOWRANK) return x.precision;
+    return x.precision == SSM_TF32X3 ? (int)SSM_TF32X3 : 0;
+  };
+  const int pa = norm_prec(a), pb = norm_prec(b);
   const int ra = a.form == SSM_FORM_LOWRANK ? a.rank : 0;
   const int rb = b.form == SSM_FORM_LOWRANK ? b.rank : 0;
   return a.lambda == b.lambda && a.beta == b.beta && xa == xb && a.form == b.form && ra == rb &&

@@ -164,21 +164,27 @@ extern "C" ssm_status ssm_objective_noalloc(const float* K_dev, int P, int Q, co
     set_error("invalid sizes or parameters");
     return SSM_EINVAL;
   }
-  Grid g;
-  g.nx = (int)dims[0];
-  g.ny = ndim >= 2 ? (int)dims[1] : 1;
-  g.nz = ndim >= 3 ? (int)dims[2] : 1;
-  for (int d = 0; d < ndim; ++d)
+  // the voxel count is checked on the 64-bit sizes, axis by axis, before any is
+  // narrowed to int (a dimension of 2^32 + 5 must not pass as 5)
+  const int64_t max_voxels = (int64_t)kThreads * kMaxBlocks;
+  int64_t nvox = 1;
+  for (int d = 0; d < ndim; ++d) {
     if (dims[d] < 1) {
       set_error("grid dimensions must be >= 1");
       return SSM_EINVAL;
     }
-  g.N = (int64_t)g.nx * g.ny * g.nz;
-  g.ld = g.N;
-  if (g.N > (int64_t)kThreads * kMaxBlocks) {
-    set_error("ssm_objective_noalloc: at most 4194304 voxels (fixed scratch of 16384 blocks)");
-    return SSM_EINVAL;
+    if (dims[d] > max_voxels || nvox * dims[d] > max_voxels) {
+      set_error("ssm_objective_noalloc: at most 4194304 voxels (fixed scratch of 16384 blocks)");
+      return SSM_EINVAL;
+    }
+    nvox *= dims[d];
   }
+  Grid g;
+  g.nx = (int)dims[0];
+  g.ny = ndim >= 2 ? (int)dims[1] : 1;
+  g.nz = ndim >= 3 ? (int)dims[2] : 1;
+  g.N = nvox;
+  g.ld = g.N;
   if (ldm < g.N || ldf < g.N) {
     set_error("leading dimension smaller than N");
     return SSM_EINVAL;

@@ -12,7 +12,8 @@
 //     kernel of ssm_tc_update.cu applies the element-wise steps;
 //   - fused, staged epilogue: the epilogue warps apply the steps to each accumulator tile
 //     straight out of TMEM, reading z, its neighbour rows, d and h from a shared-memory
-//     ring that a producer warp fills by TMA (fits up to width 224, 192 on 3D grids);
+//     ring that a producer warp fills by TMA (every width on 1D/2D grids, up to 224 on
+//     3D grids; at the widest of these, d and h are prefetched into registers instead);
 //   - fused, register epilogue: the same, with the reads software-pipelined in
 //     registers (any width).
 // In the fused forms M w never goes to memory, and the element-wise work runs while the

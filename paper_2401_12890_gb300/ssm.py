@@ -24,7 +24,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ssm.h")
 SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENAN, SSM_ETIMEOUT, SSM_EUNSUPPORTED, \
     SSM_ENOTCONVERGED, SSM_EPENDING = range(9)
 FORMS = {"lowrank": 0, "dense": 1, "admm": 2}
-PRECISIONS = {"fp32": 0, "bf16x3": 1}
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "tf32x3": 2}
 
 
 class SsmParams(ctypes.Structure):
@@ -45,6 +45,9 @@ class SsmInfo(ctypes.Structure):
         ("gram_side", ctypes.c_int), ("xi_p", ctypes.c_double), ("dtd_norm", ctypes.c_double),
         ("sigma1", ctypes.c_double), ("res_primal", ctypes.c_double),
         ("res_change", ctypes.c_double), ("plan_ms", ctypes.c_double),
+        ("hess_norm", ctypes.c_double), ("kk_norm", ctypes.c_double),
+        ("dtd_norm_power", ctypes.c_double), ("power_iters", ctypes.c_int),
+        ("power_converged", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -133,6 +136,7 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_solve_host.argtypes = [vp, fp, i64, fp, i64, ctypes.POINTER(SsmInfo), vp]
     lib.ssm_objective.argtypes = [vp, fp, i64, fp, i64, ctypes.c_int, dp, vp]
     lib.ssm_plan_factors.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
+    lib.ssm_plan_info.argtypes = [vp, ctypes.POINTER(SsmInfo)]
     lib.ssm_destroy.argtypes = [vp]
     lib.ssm_objective_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, i64, vp, i64,
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
@@ -169,7 +173,8 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_last_error.restype = ctypes.c_char_p
     lib.ssm_launch_count.restype = ctypes.c_int64
     for name in ("ssm_default_params", "ssm_plan", "ssm_solve", "ssm_solve_host",
-                 "ssm_objective", "ssm_plan_factors", "ssm_destroy", "ssm_profile_enable",
+                 "ssm_objective", "ssm_plan_factors", "ssm_plan_info", "ssm_destroy",
+                 "ssm_profile_enable",
                  "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
                  "ssm_plan_ex", "ssm_server_submit_device", "ssm_plan_set_beta",
                  "ssm_tune_beta", "ssm_plan_launch_info", "ssm_plan_set_mask",
@@ -369,6 +374,14 @@ class Plan:
         if st != SSM_OK:
             raise SsmError(st, "ssm_objective")
         return J.value
+
+    def info(self):
+        """Plan-level ssm_info fields (rank, xi_p, sigma1, the power-iteration results)."""
+        out = SsmInfo()
+        st = load_library().ssm_plan_info(self._h, ctypes.byref(out))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_plan_info")
+        return out.as_dict()
 
     def factors(self, with_vr=True):
         n = min(self.P, self.Q)

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import ladmm as oracle_ladmm
 from paper_2401_12890_gb300 import ssm, synth
 
 pytestmark = pytest.mark.gpu
@@ -56,6 +57,38 @@ def test_matches_planned_objective_on_two_calls(lib):
     plan2.close()
     st, J2 = noalloc_objective(lib, K32, M2, F2, (7, 9), 0.3, pairs=1)
     assert st == ssm.SSM_OK and J2 == pytest.approx(J2_plan, rel=2e-6)
+
+
+def _oracle_objective(K32, Md, Fd, dims, lam, pairs):
+    """Eq. 7 / Eq. 8 in FP64 on the host from the same FP32 buffers (the oracle)."""
+    K = K32.cpu().double().numpy()
+    M = Md.cpu().double().numpy()
+    F = Fd.cpu().double().numpy()
+    return oracle_ladmm.objective(K, M, F, dims, lam, pairs)
+
+
+@pytest.mark.parametrize("dims,pairs", [((5, 4, 3), 2), ((5, 4, 3), 1), ((6, 7), 2),
+                                        ((11,), 2)])
+def test_matches_the_oracle_on_1d_2d_3d_grids(lib, dims, pairs):
+    rng = np.random.default_rng(7 + len(dims) + pairs)
+    P, Q = 9, 13
+    N = int(np.prod(dims))
+    K32 = torch.from_numpy(rng.uniform(0.0, 1.0, (P, Q)).astype(np.float32)).cuda()
+    Md = torch.from_numpy(rng.uniform(0.0, 2.0, (P, N)).astype(np.float32)).cuda()
+    Fd = torch.from_numpy(rng.uniform(0.0, 1.0, (Q, N)).astype(np.float32)).cuda()
+    J_ref = _oracle_objective(K32, Md, Fd, dims, 0.37, pairs)
+    for _ in range(2):                      # a second call on the same shared scratch
+        st, J = noalloc_objective(lib, K32, Md, Fd, dims, 0.37, pairs)
+        assert st == ssm.SSM_OK
+        # FP32 product K F with FP32 accumulation over Q = 13 terms, FP64 sums
+        assert J == pytest.approx(J_ref, rel=1e-6)
+
+
+def test_rejects_dimensions_that_do_not_fit_an_int(lib):
+    K32 = torch.ones((2, 2), device="cuda")
+    for dims in ((2 ** 32 + 5,), (2 ** 32 + 5, 1), (1, 2 ** 33 + 1), (4096, 4096, 4096)):
+        st, _ = noalloc_objective(lib, K32, K32, K32, dims, 0.1)
+        assert st == ssm.SSM_EINVAL
 
 
 def test_rejects_grids_beyond_the_fixed_scratch(lib):
