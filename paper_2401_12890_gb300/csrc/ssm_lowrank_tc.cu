@@ -19,24 +19,32 @@
 // (the chunk's rows of V and of V^T) are TMA boxes in the 128-byte-swizzled K-major layout.
 //
 // Precision (TF32x3): each operand x is split as x_hi = tf32(x), x_lo = tf32(x - x_hi)
-// (round to nearest), and each product is accumulated as hi.hi + hi.lo + lo.hi (the
-// dropped lo.lo term is ~2^-22 relative). The chain of MMAs into one accumulator is kept
-// short: product 1 sums RP ranks; product 2 starts from zero for every chunk, and its
-// 32-compartment partial sums are added into FP32 registers with round-to-nearest
-// (the tensor core's accumulation does not round to nearest, and a chain over all Q
-// compartments would bias u').
+// (round to nearest), and each product is formed as hi.hi + (hi.lo + lo.hi) (the dropped
+// lo.lo term is ~2^-22 relative). The tensor core's FP32 accumulation does not round to
+// nearest, so every chain of MMAs into one accumulator is kept short and the two parts
+// go to separate accumulators: the main term hi.hi (one MMA per K step of 8) and the
+// correction hi.lo + lo.hi (~2^-11 smaller, so its own accumulation error is negligible),
+// added in FP32 registers with round-to-nearest. Product 2 starts from zero for every
+// chunk and its 32-compartment partial sums are added into registers the same way (a
+// chain over all Q compartments would bias u').
 //
-// Schedule (persistent, one CTA per SM): the work is the flattened list of (voxel tile,
-// compartment chunk) units; each CTA takes an equal contiguous share, split into
-// segments at tile boundaries. Warp roles:
+// Schedule (one CTA per SM): the work units are (segment, tile) pairs, segment-major,
+// dealt round-robin to the CTAs; a segment is a contiguous run of a tile's chunks (one
+// segment per tile when there are at least as many tiles as CTAs, several otherwise).
+// CTAs running together therefore hold the same chunks of consecutive tiles, and the
+// neighbour rows each of them stages were just read by another: L2 hits. Each segment
+// writes its partial u' to its own slot; the next iteration sums a tile's slots in
+// segment order (fixed, hence deterministic). Warp roles:
 //   warp 0      TMA: per chunk, z with its x halo, the -+nx (-+nx*ny) neighbour rows and
 //               the chunk's V / V^T boxes (hi and lo) into a ring of NS stages
 //   warp 1      MMA: product 1 of chunk g, then product 2 of chunk g-1 (so the tensor
 //               core works ahead of the epilogue); commits release stages and buffers
-//   warps 2-9   epilogue, two per TMEM lane quarter, each half of a chunk's compartments:
-//               tcgen05.ld of V a, the z-step and dual step, z' (and d') stores, w split
-//               into TMEM, and the running sum of product 2 in registers
-// TMEM: V a and w are double-buffered by chunk parity, a is per segment, U by parity.
+//   warps 2-17  epilogue, four per TMEM lane quarter, each a quarter of a chunk's
+//               compartments: tcgen05.ld of V a, the z-step and dual step, z' (and d')
+//               stores, w split into TMEM, and the running sum of product 2 in registers
+// Waiting warps sleep in mbarrier.try_wait (with a suspend-time hint) instead of polling.
+// TMEM: V a (main, correction) and w (hi, lo) are double-buffered by chunk parity, a is
+// per segment, U (main, correction) is double-buffered for RP = 32 and single for 64.
 // HBM traffic per state element and iteration: read z, write z' (8 B); per voxel and rank:
 // S, the partial u in and out. Every mbarrier wait is bounded and reports SSM_ETIMEOUT
 // through the plan's device error word; the TMA warp waits (bounded) for its last copies
@@ -52,45 +60,67 @@ namespace {
 
 constexpr int TV = 128;              // voxels per tile: MMA M, TMEM lanes
 constexpr int QC = 32;               // compartments per chunk
-constexpr int HC = QC / 2;           // compartments per epilogue warp and chunk
-constexpr int NEPI = 8;              // epilogue warps (two per TMEM lane quarter)
-constexpr int NT = 32 * (2 + NEPI);
+// epilogue warps: 8 on 1D/2D grids, 16 on 3D grids (whose elements read four neighbour
+// rows: more warps hide their longer latency chains); EPQ per TMEM lane quarter, each
+// taking GC compartments of a chunk
+template <int NR> struct Epi {
+  static constexpr int NEPI = NR == 4 ? 16 : 8;
+  static constexpr int EPQ = NEPI / 4;
+  static constexpr int GC = 32 / EPQ;
+  static constexpr int NT = 32 * (2 + NEPI);
+  static_assert(NEPI % 4 == 0 && GC % 8 == 0, "epilogue split");
+};
 constexpr int ZW = TV + 8;           // staged z row: voxels n0-4 .. n0+TV+3
 constexpr int NW = TV + 4;           // staged neighbour row: 4-aligned base .. +TV+3
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int kSmemLimit = 227 * 1024;
+constexpr int kPrefetch = 8;         // chunks of a tile's own z rows prefetched into L2 ahead
 
-// TMEM column map (RP-independent part)
-constexpr uint32_t T_VA = 0;         // V a: chunk parity p at 32 p
-constexpr uint32_t T_W = 64;         // w: parity p at 64 + 64 p (hi), +32 (lo)
-constexpr uint32_t T_A = 192;        // a: hi at 192, lo at 192 + RP
-
+// Rings, buffers and tensor-memory columns of one kernel configuration.
+//   V ring (NSV stages): the chunk's V boxes (B of product 1) and V^T boxes (B of product
+//     2), hi and lo; a stage is held from its load until product 2 of its chunk completes
+//   z ring (NSZ stages): z with its x halo and the NR neighbour rows; held until the
+//     epilogue warps have read it
+//   TMEM: V a in NVA buffers (main and correction, 64 columns each), w in 2 (hi and lo),
+//     a (hi and lo, per segment), U in UB buffers (main and correction, 2 RP columns)
+// Product 1 runs NVA - 1 chunks ahead of the epilogue and the epilogue reads product 2's
+// sums two chunks late, so neither MMA latency is on the epilogue's path.
 template <int RP, int NR>
 struct Lay {
+  static constexpr int NVA = RP == 32 ? 3 : 2;
+  static constexpr int UB = RP == 32 ? 2 : 1;
   static constexpr int V1 = RP / 32 * QC * 128;   // V rows of the chunk: RP/32 swizzle atoms
   static constexpr int V2 = RP * 128;            // V^T rows (RP) x the chunk (128 bytes)
   static constexpr int v1h = 0, v1l = V1, v2h = 2 * V1, v2l = 2 * V1 + V2;
-  static constexpr int zc = 2 * V1 + 2 * V2;
-  static constexpr int zn = zc + QC * ZW * 4;
-  static constexpr int raw = zn + NR * QC * NW * 4;
-  static constexpr int stage = (raw + 1023) / 1024 * 1024;
+  static constexpr int VST = 2 * V1 + 2 * V2;    // V stage (a multiple of 1024)
+  static constexpr int zc = 0;
+  static constexpr int zn = QC * ZW * 4;
+  static constexpr int ZST = (zn + NR * QC * NW * 4 + 1023) / 1024 * 1024;
   static constexpr int RESERVE = 1024 + 512;     // alignment slack, barriers, TMEM slot
   static constexpr int STATIC_MAX = 1024;       // the residual variant's reduction array
-  static constexpr int ns_fit = (kSmemLimit - RESERVE - STATIC_MAX) / stage;
-  static constexpr int NS = ns_fit > 4 ? 4 : ns_fit;
-  static constexpr bool valid = NS >= 2;
-  static constexpr int bytes = (NS < 1 ? 1 : NS) * stage + RESERVE;
-  static constexpr uint32_t T_U = T_A + 2 * RP;  // U: parity p at T_U + RP p
+  static constexpr int budget = kSmemLimit - RESERVE - STATIC_MAX;
+  static constexpr int nsz_with(int nsv) { return (budget - nsv * VST) / ZST; }
+  static constexpr int NSV = nsz_with(NVA + 1) >= 2 ? NVA + 1 : NVA;
+  static constexpr int NSZ = nsz_with(NSV) > 4 ? 4 : nsz_with(NSV);
+  static constexpr bool valid = NSZ >= 2 && NSV >= 2;
+  static constexpr int zbase = NSV * VST;        // the z ring after the V ring
+  static constexpr int bytes = (valid ? zbase + NSZ * ZST : 0) + RESERVE;
+  static constexpr unsigned VBYTES = (unsigned)VST;
+  static constexpr unsigned ZBYTES = (unsigned)(QC * ZW * 4 + NR * QC * NW * 4);
+  static constexpr uint32_t T_VA = 0;                     // buffer b: main 64 b, corr +32
+  static constexpr uint32_t T_W = 64 * NVA;               // buffer p: hi 64 p, lo +32
+  static constexpr uint32_t T_A = T_W + 128;              // hi, lo at + RP
+  static constexpr uint32_t T_U = T_A + 2 * RP;           // buffer b: main 2 RP b, corr + RP
   // kind::tf32 instruction descriptors: D = F32 (bits 4-5 = 1), A = B = TF32 (bits 7-9,
   // 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
   static constexpr uint32_t IDESC1 = (1u << 4) | (2u << 7) | (2u << 10) |
                                      ((uint32_t)(QC >> 3) << 17) | ((uint32_t)(TV >> 4) << 24);
   static constexpr uint32_t IDESC2 = (1u << 4) | (2u << 7) | (2u << 10) |
                                      ((uint32_t)(RP >> 3) << 17) | ((uint32_t)(TV >> 4) << 24);
-  static_assert(zc % 1024 == 0 && zn % 128 == 0 && v1l % 1024 == 0 && v2h % 1024 == 0 &&
-                    v2l % 1024 == 0,
+  static_assert(VST % 1024 == 0 && ZST % 1024 == 0 && zn % 128 == 0 && v1l % 1024 == 0 &&
+                    v2h % 1024 == 0 && v2l % 1024 == 0,
                 "layout");
-  static_assert(T_U + 2 * RP <= TMEM_COLS, "tensor memory");
+  static_assert(T_U + 2 * RP * UB <= TMEM_COLS, "tensor memory");
 };
 
 struct LrtcMaps {
@@ -101,14 +131,15 @@ struct LrtcMaps {
 
 struct LrtcArgs {
   float* __restrict__ Zout;
-  float* __restrict__ Dout;         // d^{k+1}, written when write_d != 0
+  float* __restrict__ Dout;         // d^{k+1} (iterations before a residual test)
   const float* __restrict__ Din;    // d^k (residual-test iterations)
   const float* __restrict__ S;      // RP x ld
   const float* __restrict__ Pin;    // partial u of the previous iteration [tile][seg][RP][TV]
   float* __restrict__ Pout;         // partial u of this iteration
-  int64_t ntiles, T;                // tiles, units (ntiles * nch)
-  int nch;                          // chunks per tile
-  int maxseg;                       // segment slots per tile
+  int64_t ntiles;                   // voxel tiles
+  int nch;                          // compartment chunks per tile
+  int spc;                          // segments per tile (each a contiguous run of chunks)
+  int kr;                           // K steps of 8 ranks holding the rank r (<= RP / 8)
   const float* __restrict__ coefA;  // RP
   const float* __restrict__ coefW;  // RP
   double* __restrict__ partial;     // 4 doubles per block (check iterations)
@@ -116,25 +147,19 @@ struct LrtcArgs {
   int* __restrict__ err;            // device error word
   Grid g;
   int Q;
-  int write_d;
   float beta, inv_beta, xi, lam_s, inv_xb;
 };
 
 __host__ __device__ __forceinline__ int64_t floor4(int64_t v) {
   return v >= 0 ? (v & ~(int64_t)3) : -(((-v) + 3) & ~(int64_t)3);
 }
-__host__ __device__ __forceinline__ int64_t share_lo(int64_t T, int64_t j, int64_t G) {
-  return (T * j) / G;
-}
-// the first CTA whose share contains unit u
-__host__ __device__ __forceinline__ int64_t owner_of(int64_t u, int64_t T, int64_t G) {
-  return ((u + 1) * G + T - 1) / T - 1;
-}
 
+// x rounded to TF32 (10 stored mantissa bits), to nearest with ties away from zero: add
+// half a unit of the last kept place to the magnitude bits and clear the 13 bits below
+// (a carry into the exponent is the correct rounding up; finite inputs of magnitude
+// below 2^128 (1 - 2^-12) stay finite)
 __device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // shared-memory descriptor, K-major operand in the 128-byte swizzle layout (8 rows x
@@ -168,52 +193,54 @@ __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 16 consecutive 32-bit TMEM columns of this warp's 32 lanes (one lane per thread)
-__device__ __forceinline__ void tld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 8 consecutive 32-bit TMEM columns of this warp's 32 lanes (one lane per thread)
+__device__ __forceinline__ void tld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
+        "=r"(r[7])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tst16(uint32_t taddr, const float* v) {
+__device__ __forceinline__ void tst8(uint32_t taddr, const float* v) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16};\n" ::"r"(taddr),
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(
+          taddr),
       "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
       "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-      "r"(__float_as_uint(v[15]))
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
       : "memory");
 }
 __device__ __forceinline__ void tst_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-template <int RP, int NR, bool CHECK>
-__global__ void __launch_bounds__(NT, 1) lrtc_kernel(const __grid_constant__ LrtcMaps maps,
-                                                     const LrtcArgs a) {
+template <int RP, int NR, bool CHECK, bool WD>
+__global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_constant__ LrtcMaps maps,
+                                                              const LrtcArgs a) {
   using L = Lay<RP, NR>;
-  constexpr int NS = L::NS;
-  constexpr int RH = RP / 2;          // ranks per epilogue half
+  constexpr int NEPI = Epi<NR>::NEPI, EPQ = Epi<NR>::EPQ, GC = Epi<NR>::GC, NT = Epi<NR>::NT;
+  constexpr int NSV = L::NSV, NSZ = L::NSZ, NVA = L::NVA, UB = L::UB;
+  constexpr int D1 = NVA - 1;         // chunks product 1 runs ahead of product 2
+  constexpr int RQ = RP / EPQ;        // ranks per epilogue warp of a lane quarter
   static_assert(L::valid, "two ring stages");
+  static_assert(RQ % 8 == 0, "rank split");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * L::stage);
-  uint64_t* empty = full + NS;
-  uint64_t* va_full = empty + NS;
-  uint64_t* va_free = va_full + 2;
-  uint64_t* w_full = va_free + 2;
+  unsigned char* vring = smem;
+  unsigned char* zring = smem + L::zbase;
+  uint64_t* vfull = reinterpret_cast<uint64_t*>(zring + NSZ * L::ZST);
+  uint64_t* vempty = vfull + NSV;
+  uint64_t* zfull = vempty + NSV;
+  uint64_t* zempty = zfull + NSZ;
+  uint64_t* va_full = zempty + NSZ;
+  uint64_t* va_free = va_full + NVA;
+  uint64_t* w_full = va_free + NVA;
   uint64_t* u_full = w_full + 2;
   uint64_t* u_free = u_full + 2;
   uint64_t* a_ready = u_free + 2;
@@ -221,19 +248,23 @@ __global__ void __launch_bounds__(NT, 1) lrtc_kernel(const __grid_constant__ Lrt
   uint64_t* fin = a_free + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t G = gridDim.x;
-  const int64_t lo = share_lo(a.T, blockIdx.x, G);
-  const int64_t hi = share_lo(a.T, blockIdx.x + 1, G);
-  const int nch = a.nch;
+  const int64_t nunits = a.ntiles * a.spc;
+  const int nch = a.nch, spc = a.spc;
 
   if (tid == 0) {
-    for (int s = 0; s < NS; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1 + NEPI);
+    for (int s = 0; s < NSV; ++s) {
+      mbar_init(&vfull[s], 1);
+      mbar_init(&vempty[s], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int s = 0; s < NSZ; ++s) {
+      mbar_init(&zfull[s], 1);
+      mbar_init(&zempty[s], NEPI);
+    }
+    for (int i = 0; i < NVA; ++i) {
       mbar_init(&va_full[i], 1);
       mbar_init(&va_free[i], NEPI);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&w_full[i], NEPI);
       mbar_init(&u_full[i], 1);
       mbar_init(&u_free[i], NEPI);
@@ -262,6 +293,14 @@ __global__ void __launch_bounds__(NT, 1) lrtc_kernel(const __grid_constant__ Lrt
   // neighbour rows beyond x: -nx, +nx, -nx*ny, +nx*ny (the y pair first when there is one)
   const int64_t off[4] = {ny > 1 ? -(int64_t)nx : -plane, ny > 1 ? (int64_t)nx : plane, -plane,
                           plane};
+  // unit u = (segment s, tile t), segment-major: the CTAs running together hold the
+  // same chunks of consecutive tiles, so the neighbour rows they stage are L2 hits
+  auto unit_of = [&](int64_t u, int64_t& tile, int& c0, int& c1, int& sg) {
+    sg = (int)(u / a.ntiles);
+    tile = u - (int64_t)sg * a.ntiles;
+    c0 = (int)((int64_t)sg * nch / spc);
+    c1 = (int)((int64_t)(sg + 1) * nch / spc);
+  };
 
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
@@ -270,112 +309,133 @@ __global__ void __launch_bounds__(NT, 1) lrtc_kernel(const __grid_constant__ Lrt
       tma_prefetch_map(&maps.zn);
       tma_prefetch_map(&maps.v1h);
       tma_prefetch_map(&maps.v2h);
-      constexpr unsigned bytes = (unsigned)(2 * L::V1 + 2 * L::V2 + QC * ZW * 4 + NR * QC * NW * 4);
       int g = 0;
-      for (int64_t u = lo; u < hi && !failed;) {
-        const int64_t tile = u / nch;
-        const int c0 = (int)(u - tile * nch);
-        const int cend = (int)(min(hi - tile * nch, (int64_t)nch));
+      for (int64_t u = blockIdx.x; u < nunits && !failed; u += gridDim.x) {
+        int64_t tile;
+        int c0, c1, sg;
+        unit_of(u, tile, c0, c1, sg);
         const int64_t n0 = tile * TV;
-        for (int c = c0; c < cend; ++c, ++g) {
-          const int s = g % NS, k = g / NS;
-          if (k > 0 && !mbar_wait(&empty[s], (k - 1) & 1)) {
+        // the tile's own z rows come from HBM: they are prefetched into L2 kPrefetch chunks
+        // ahead of their staged loads, so that enough bytes are in flight per SM (the
+        // staged loads and the neighbour rows, which other CTAs prefetched, hit L2)
+        for (int c = c0 + 1; c < c0 + kPrefetch && c < c1; ++c)
+          tma_prefetch_2d(&maps.zc, (int)(n0 - 4), c * QC);
+        for (int c = c0; c < c1; ++c, ++g) {
+          const int q0 = c * QC;
+          if (c + kPrefetch < c1) tma_prefetch_2d(&maps.zc, (int)(n0 - 4), q0 + kPrefetch * QC);
+          // the chunk's V boxes (product 1 needs them first)
+          const int sv = g % NSV, kv = g / NSV;
+          if (kv > 0 && !mbar_wait_sleep(&vempty[sv], (kv - 1) & 1)) {
             failed = true;
             break;
           }
-          unsigned char* st = smem + s * L::stage;
-          const int q0 = c * QC;
-          mbar_arrive_expect_tx(&full[s], bytes);
+          unsigned char* vs = vring + sv * L::VST;
+          mbar_arrive_expect_tx(&vfull[sv], L::VBYTES);
 #pragma unroll
           for (int at = 0; at < RP / 32; ++at) {
-            tma_load_2d(st + L::v1h + at * QC * 128, &maps.v1h, at * 32, q0, &full[s]);
-            tma_load_2d(st + L::v1l + at * QC * 128, &maps.v1l, at * 32, q0, &full[s]);
+            tma_load_2d(vs + L::v1h + at * QC * 128, &maps.v1h, at * 32, q0, &vfull[sv]);
+            tma_load_2d(vs + L::v1l + at * QC * 128, &maps.v1l, at * 32, q0, &vfull[sv]);
           }
-          tma_load_2d(st + L::v2h, &maps.v2h, q0, 0, &full[s]);
-          tma_load_2d(st + L::v2l, &maps.v2l, q0, 0, &full[s]);
-          tma_load_2d(st + L::zc, &maps.zc, (int)(n0 - 4), q0, &full[s]);
+          tma_load_2d(vs + L::v2h, &maps.v2h, q0, 0, &vfull[sv]);
+          tma_load_2d(vs + L::v2l, &maps.v2l, q0, 0, &vfull[sv]);
+          // z with its x halo and the neighbour rows
+          const int sz = g % NSZ, kz = g / NSZ;
+          if (kz > 0 && !mbar_wait_sleep(&zempty[sz], (kz - 1) & 1)) {
+            failed = true;
+            ++g;          // the V copies of this chunk were issued
+            break;
+          }
+          unsigned char* zs = zring + sz * L::ZST;
+          mbar_arrive_expect_tx(&zfull[sz], L::ZBYTES);
+          tma_load_2d(zs + L::zc, &maps.zc, (int)(n0 - 4), q0, &zfull[sz]);
 #pragma unroll
           for (int j = 0; j < NR; ++j)
-            tma_load_2d(st + L::zn + j * QC * NW * 4, &maps.zn, (int)floor4(n0 + off[j]), q0,
-                        &full[s]);
+            tma_load_2d(zs + L::zn + j * QC * NW * 4, &maps.zn, (int)floor4(n0 + off[j]), q0,
+                        &zfull[sz]);
         }
-        u = tile * nch + cend;
       }
       // no copy may still be in flight when the CTA exits: wait (bounded) for the last
       // phase issued into every stage
-      for (int s = 0; s < NS && s < g; ++s) {
-        const int last = s + ((g - 1 - s) / NS) * NS;
-        mbar_wait(&full[s], (last / NS) & 1);
-      }
+      for (int s = 0; s < NSV && s < g; ++s)
+        mbar_wait_sleep(&vfull[s], ((s + ((g - 1 - s) / NSV) * NSV) / NSV) & 1);
+      for (int s = 0; s < NSZ && s < g; ++s)
+        mbar_wait_sleep(&zfull[s], ((s + ((g - 1 - s) / NSZ) * NSZ) / NSZ) & 1);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t a_hi = tmem + T_A, a_lo = tmem + T_A + RP;
+      const uint32_t a_hi = tmem + L::T_A, a_lo = tmem + L::T_A + RP;
+      // product 2 of chunk gg: U (main, correction) = w (hi, lo) . V_c (hi, lo)
       auto product2 = [&](int gg) {
-        const int p = gg & 1, ph = gg >> 1;
-        if (!failed && !mbar_wait(&w_full[p], ph & 1)) failed = true;
-        if (!failed && gg >= 2 && !mbar_wait(&u_free[p], (ph - 1) & 1)) failed = true;
+        const int p = gg & 1;
+        if (!failed && !mbar_wait_sleep(&w_full[p], (gg >> 1) & 1)) failed = true;
+        // the U buffer is free once the epilogue has read chunk gg - UB's
+        const int gp = gg - UB;
+        if (!failed && gp >= 0 && !mbar_wait_sleep(&u_free[gp & 1], (gp >> 1) & 1))
+          failed = true;
         if (failed) return;
         fence_after();
-        const uint32_t st = smem_u32(smem + (gg % NS) * L::stage);
-        const uint32_t d = tmem + L::T_U + RP * p;
-        const uint32_t w_hi = tmem + T_W + 64 * p, w_lo = w_hi + 32;
+        const uint32_t vs = smem_u32(vring + (gg % NSV) * L::VST);
+        const uint32_t dm = tmem + L::T_U + 2 * RP * (gg % UB), dc = dm + RP;
+        const uint32_t w_hi = tmem + L::T_W + 64 * p, w_lo = w_hi + 32;
 #pragma unroll
         for (int k = 0; k < QC / 8; ++k) {
-          const uint64_t bh = sdesc(st + L::v2h + k * 32), bl = sdesc(st + L::v2l + k * 32);
-          mma_tf32(d, w_hi + 8 * k, bh, L::IDESC2, k > 0 ? 1u : 0u);
-          mma_tf32(d, w_hi + 8 * k, bl, L::IDESC2, 1u);
-          mma_tf32(d, w_lo + 8 * k, bh, L::IDESC2, 1u);
+          const uint64_t bh = sdesc(vs + L::v2h + k * 32), bl = sdesc(vs + L::v2l + k * 32);
+          mma_tf32(dm, w_hi + 8 * k, bh, L::IDESC2, k > 0 ? 1u : 0u);
+          mma_tf32(dc, w_hi + 8 * k, bl, L::IDESC2, k > 0 ? 1u : 0u);
+          mma_tf32(dc, w_lo + 8 * k, bh, L::IDESC2, 1u);
         }
         commit(&u_full[p]);
-        commit(&empty[gg % NS]);
+        commit(&vempty[gg % NSV]);    // the V stage is free once these complete
       };
       int g = 0, si = 0;
-      for (int64_t u = lo; u < hi && !failed;) {
-        const int64_t tile = u / nch;
-        const int c0 = (int)(u - tile * nch);
-        const int cend = (int)(min(hi - tile * nch, (int64_t)nch));
-        const int nchk = cend - c0;
-        if (!mbar_wait(a_ready, si & 1)) {
+      for (int64_t u = blockIdx.x; u < nunits && !failed; u += gridDim.x) {
+        int64_t tile;
+        int c0, c1, sg;
+        unit_of(u, tile, c0, c1, sg);
+        const int nchk = c1 - c0;
+        if (!mbar_wait_sleep(a_ready, si & 1)) {
           failed = true;
           break;
         }
         fence_after();
         for (int i = 0; i < nchk && !failed; ++i) {
-          const int gg = g + i, s = gg % NS, p = gg & 1, ph = gg >> 1;
-          if (!mbar_wait(&full[s], (gg / NS) & 1)) failed = true;
-          if (!failed && gg >= 2 && !mbar_wait(&va_free[p], (ph - 1) & 1)) failed = true;
+          // product 1 of chunk gg: V a (main, correction) = a (hi, lo) . V_c^T (hi, lo)
+          const int gg = g + i, b = gg % NVA;
+          if (!mbar_wait_sleep(&vfull[gg % NSV], (gg / NSV) & 1)) failed = true;
+          if (!failed && gg >= NVA && !mbar_wait_sleep(&va_free[b], ((gg / NVA) - 1) & 1))
+            failed = true;
           if (failed) break;
           fence_after();
-          const uint32_t st = smem_u32(smem + s * L::stage);
-          const uint32_t d = tmem + T_VA + 32 * p;
-#pragma unroll
-          for (int k = 0; k < RP / 8; ++k) {
+          const uint32_t vs = smem_u32(vring + (gg % NSV) * L::VST);
+          const uint32_t dm = tmem + L::T_VA + 64 * b, dc = dm + 32;
+          // the padding ranks beyond r carry zero a: their K steps are skipped
+#pragma unroll 4
+          for (int k = 0; k < a.kr; ++k) {
             const int at = k / 4, o = (k % 4) * 32;
-            const uint64_t bh = sdesc(st + L::v1h + at * QC * 128 + o);
-            const uint64_t bl = sdesc(st + L::v1l + at * QC * 128 + o);
-            mma_tf32(d, a_hi + 8 * k, bh, L::IDESC1, k > 0 ? 1u : 0u);
-            mma_tf32(d, a_hi + 8 * k, bl, L::IDESC1, 1u);
-            mma_tf32(d, a_lo + 8 * k, bh, L::IDESC1, 1u);
+            const uint64_t bh = sdesc(vs + L::v1h + at * QC * 128 + o);
+            const uint64_t bl = sdesc(vs + L::v1l + at * QC * 128 + o);
+            mma_tf32(dm, a_hi + 8 * k, bh, L::IDESC1, k > 0 ? 1u : 0u);
+            mma_tf32(dc, a_hi + 8 * k, bl, L::IDESC1, k > 0 ? 1u : 0u);
+            mma_tf32(dc, a_lo + 8 * k, bh, L::IDESC1, 1u);
           }
-          commit(&va_full[p]);
+          commit(&va_full[b]);
           if (i == nchk - 1) commit(a_free);     // a may be rewritten once these complete
-          if (i > 0) product2(gg - 1);
+          if (i >= D1) product2(gg - D1);
         }
-        if (!failed) product2(g + nchk - 1);
+        // the segment's last products 2
+        for (int j = (nchk > D1 ? nchk - D1 : 0); j < nchk && !failed; ++j) product2(g + j);
         g += nchk;
         ++si;
-        u = tile * nch + cend;
       }
       // every product issued has completed before the TMEM is freed
       commit(fin);
-      mbar_wait(fin, 0);
+      mbar_wait_sleep(fin, 0);
     }
   } else {
     // ------------------------------------------------------------------ epilogue warps
     const int quarter = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int grp = (warp - 2) >> 2;                 // compartments grp*GC .. of a chunk
     const int v = quarter * 32 + lane;               // voxel within the tile = TMEM lane
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     const int64_t ld = a.g.ld, N = a.g.N;
@@ -383,21 +443,23 @@ __global__ void __launch_bounds__(NT, 1) lrtc_kernel(const __grid_constant__ Lrt
     const bool zl = nz > 1 && a.g.zlink;
     const float c2 = a.lam_s * a.inv_xb;             // weight of the neighbour sum
     const float c3 = a.beta * a.inv_xb;              // weight of V a
+    const float beta = a.beta, inv_beta = a.inv_beta;
     int g = 0, si = 0;
-    for (int64_t u = lo; u < hi;) {
-      const int64_t tile = u / nch;
-      const int c0 = (int)(u - tile * nch);
-      const int cend = (int)(min(hi - tile * nch, (int64_t)nch));
-      const int nchk = cend - c0;
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+      int64_t tile;
+      int c0, c1, sg;
+      unit_of(u, tile, c0, c1, sg);
+      const int nchk = c1 - c0;
       const int64_t n0 = tile * TV;
       const int64_t n = n0 + v;
       const bool valid = n < N;
+      // voxel coordinates in 32-bit arithmetic (N < 2^31)
       int x = 0, y = 0, zc = 0;
       if (valid) {
-        x = (int)(n % nx);
-        const int64_t t = n / nx;
-        y = (int)(t % ny);
-        zc = (int)(t / ny);
+        const unsigned nn = (unsigned)n, t = nn / (unsigned)nx;
+        x = (int)(nn - t * (unsigned)nx);
+        y = (int)(t % (unsigned)ny);
+        zc = (int)(t / (unsigned)ny);
       }
       // a voxel outside the object is left alone (its z stays 0) and is nobody's neighbour
       const uint8_t* mk = a.mask;
@@ -410,135 +472,192 @@ __global__ void __launch_bounds__(NT, 1) lrtc_kernel(const __grid_constant__ Lrt
       const bool hzp = zl && in && zc < nz - 1 && (!mk || mk[n + plane]);
       const float deg = (float)(hxm + hxp + hym + hyp + hzm + hzp);
       const float e1 = (a.xi + a.beta - a.lam_s * deg) * a.inv_xb;   // weight of z
+      // neighbour presence as 0/1 weights: the staged rows are always readable (finite
+      // z values or the copy's zero fill), so every neighbour term is a fused add
+      const float fxm = hxm ? 1.f : 0.f, fxp = hxp ? 1.f : 0.f;
       int nidx[4];
-      bool nok[4];
+      float fk[4];
       {
         const bool flags[4] = {ny > 1 ? hym : hzm, ny > 1 ? hyp : hzp, hzm, hzp};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           nidx[j] = j < NR ? (int)(n + off[j] - floor4(n0 + off[j])) : 0;
-          nok[j] = j < NR && flags[j];
+          fk[j] = (j < NR && flags[j]) ? 1.f : 0.f;
         }
       }
-      // a for this half's ranks: a_i = S_i/(beta + sigma_i^2) - W_i u_i, u_i summed over
+      // a for this warp's ranks: a_i = S_i/(beta + sigma_i^2) - W_i u_i, u_i summed over
       // the tile's segment slots of the previous iteration in segment order
-      const int64_t j0 = owner_of(tile * nch, a.T, G);
-      const int nseg = (int)(owner_of(tile * nch + nch - 1, a.T, G) - j0 + 1);
-      const int sidx = (int)(blockIdx.x - j0);
-      if (si > 0 && !failed && !mbar_wait(a_free, (si - 1) & 1)) failed = true;
+      if (si > 0 && !failed && !mbar_wait_sleep(a_free, (si - 1) & 1)) failed = true;
       fence_after();
       {
-        float ah[RH], al[RH];
-        const float* pt = a.Pin + (tile * a.maxseg) * (int64_t)(RP * TV);
+        float ah[RQ], al[RQ];
+        const float* pt = a.Pin + (tile * spc) * (int64_t)(RP * TV) + grp * RQ * TV + v;
+        const float* sp = a.S + (int64_t)(grp * RQ) * ld + n;
+        // every load of the a-vector is issued before any is used
+        float us[RQ], sv[RQ];
 #pragma unroll
-        for (int i = 0; i < RH; ++i) {
-          const int r = half * RH + i;
-          float av = 0.f;
-          if (in) {
-            float us = 0.f;
-            for (int sg = 0; sg < nseg; ++sg) us += pt[(sg * RP + r) * TV + v];
-            av = __ldg(a.S + r * ld + n) * __ldg(a.coefA + r) - __ldg(a.coefW + r) * us;
-          }
+        for (int i = 0; i < RQ; ++i) {
+          sv[i] = in ? __ldg(sp + i * ld) : 0.f;
+          us[i] = in ? pt[i * TV] : 0.f;
+        }
+        for (int k = 1; k < spc; ++k) {
+#pragma unroll
+          for (int i = 0; i < RQ; ++i) us[i] += in ? pt[(k * RP + i) * TV] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < RQ; ++i) {
+          const int r = grp * RQ + i;
+          const float av = in ? sv[i] * __ldg(a.coefA + r) - __ldg(a.coefW + r) * us[i] : 0.f;
           ah[i] = tf32_rna(av);
           al[i] = tf32_rna(av - ah[i]);
         }
 #pragma unroll
-        for (int i = 0; i < RH; i += 16) {
-          tst16(tmem + lane_base + T_A + half * RH + i, ah + i);
-          tst16(tmem + lane_base + T_A + RP + half * RH + i, al + i);
+        for (int i = 0; i < RQ; i += 8) {
+          tst8(tmem + lane_base + L::T_A + grp * RQ + i, ah + i);
+          tst8(tmem + lane_base + L::T_A + RP + grp * RQ + i, al + i);
         }
         tst_wait();
       }
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(a_ready);
-      float uacc[RH];
+      float uacc[RQ];
 #pragma unroll
-      for (int i = 0; i < RH; ++i) uacc[i] = 0.f;
+      for (int i = 0; i < RQ; ++i) uacc[i] = 0.f;
+      // product 2's sums of chunk gg (main + correction, rounded to nearest in registers)
       auto consume_u = [&](int gg) {
         const int p = gg & 1;
-        if (!failed && !mbar_wait(&u_full[p], (gg >> 1) & 1)) failed = true;
+        if (!failed && !mbar_wait_sleep(&u_full[p], (gg >> 1) & 1)) failed = true;
         fence_after();
+        const uint32_t ub = tmem + lane_base + L::T_U + 2 * RP * (gg % UB) + grp * RQ;
 #pragma unroll
-        for (int i = 0; i < RH; i += 16) {
-          float uu[16];
-          tld16(tmem + lane_base + L::T_U + RP * p + half * RH + i, uu);
+        for (int i = 0; i < RQ; i += 8) {
+          float um[8], uc[8];
+          tld8(ub + i, um);
+          tld8(ub + RP + i, uc);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) uacc[i + j] += uu[j];
+          for (int j = 0; j < 8; ++j) uacc[i + j] += um[j] + uc[j];
         }
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&u_free[p]);
       };
       for (int i = 0; i < nchk; ++i) {
-        const int gg = g + i, s = gg % NS, p = gg & 1;
-        const int qh = (c0 + i) * QC + half * HC;   // this warp's first compartment
-        if (!failed && !mbar_wait(&full[s], (gg / NS) & 1)) failed = true;
-        if (!failed && !mbar_wait(&va_full[p], (gg >> 1) & 1)) failed = true;
+        const int gg = g + i, sz = gg % NSZ, b = gg % NVA, p = gg & 1;
+        const int qg = (c0 + i) * QC + grp * GC;   // this warp's first compartment
+        if (!failed && !mbar_wait_sleep(&zfull[sz], (gg / NSZ) & 1)) failed = true;
+        if (!failed && !mbar_wait_sleep(&va_full[b], (gg / NVA) & 1)) failed = true;
         fence_after();
-        float va[HC];
-        tld16(tmem + lane_base + T_VA + 32 * p + half * HC, va);
+        float va[GC];
+#pragma unroll
+        for (int j = 0; j < GC; j += 8) {
+          float vc[8];
+          tld8(tmem + lane_base + L::T_VA + 64 * b + grp * GC + j, va + j);
+          tld8(tmem + lane_base + L::T_VA + 64 * b + 32 + grp * GC + j, vc);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) va[j + k] += vc[k];
+        }
         fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&va_free[p]);
-        float dk[HC];
-        if constexpr (CHECK) {
+        if (lane == 0) mbar_arrive(&va_free[b]);
+        const bool work = in && !failed;
+        const int jn = min(GC, Q - qg);              // the same for every lane
+        const float* zcr = reinterpret_cast<const float*>(zring + sz * L::ZST + L::zc) +
+                           grp * GC * ZW + 4 + v;
+        const float* znr = reinterpret_cast<const float*>(zring + sz * L::ZST + L::zn) +
+                           grp * GC * NW;
+        float w[GC];
+        float* zp = a.Zout + (int64_t)qg * ld + n;
+        if (work) {
+          // in halves of 8 compartments: the staged rows first (all shared-memory loads of
+          // the half in flight at once, before any store to global memory), then the
+          // arithmetic, then the stores
 #pragma unroll
-          for (int j = 0; j < HC; ++j)
-            dk[j] = (in && qh + j < Q) ? __ldg(a.Din + (int64_t)(qh + j) * ld + n) : 0.f;
-        }
-        const unsigned char* st = smem + s * L::stage;
-        const float* zcr = reinterpret_cast<const float*>(st + L::zc) + half * HC * ZW;
-        const float* znr = reinterpret_cast<const float*>(st + L::zn) + half * HC * NW;
-        float wh[HC], wl[HC];
+          for (int h = 0; h < GC; h += 8) {
+            float zz[8], nb[8];
 #pragma unroll
-        for (int j = 0; j < HC; ++j) {
-          const int q = qh + j;
-          float w = 0.f;
-          if (!failed && in && q < Q) {
-            const float z = zcr[j * ZW + 4 + v];
-            float nb = 0.f;
-            if (hxm) nb += zcr[j * ZW + 3 + v];
-            if (hxp) nb += zcr[j * ZW + 5 + v];
+            for (int j = 0; j < 8; ++j) {
+              const int r = h + j;
+              zz[j] = zcr[r * ZW];
+              nb[j] = fxm * zcr[r * ZW - 1];
+              nb[j] = fmaf(fxp, zcr[r * ZW + 1], nb[j]);
 #pragma unroll
-            for (int k = 0; k < NR; ++k)
-              if (nok[k]) nb += znr[(k * QC + j) * NW + nidx[k]];
-            const float zn = fmaxf(0.f, fmaf(e1, z, fmaf(c2, nb, c3 * va[j])));
-            const float t = z + va[j];
-            w = a.beta * (2.f * zn - t);
-            const int64_t o = (int64_t)q * ld + n;
-            a.Zout[o] = zn;
-            if (a.write_d) a.Dout[o] = a.beta * (t - zn);
+              for (int k = 0; k < NR; ++k)
+                nb[j] = fmaf(fk[k], znr[(k * QC + r) * NW + nidx[k]], nb[j]);
+            }
+            float zn[8], tt[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int r = h + j;
+              zn[j] = fmaxf(0.f, fmaf(e1, zz[j], fmaf(c2, nb[j], c3 * va[r])));
+              tt[j] = zz[j] + va[r];
+              w[r] = r < jn ? beta * (2.f * zn[j] - tt[j]) : 0.f;
+            }
             if constexpr (CHECK) {
-              const float f = t - dk[j] * a.inv_beta;   // f^{k+1}
-              const float e = zn - f, ch = zn - z;
-              s1 = fmaf(e, e, s1);
-              s2 = fmaf(ch, ch, s2);
-              s3 = fmaf(zn, zn, s3);
+              // f^{k+1} = t - d^k / beta needs d^k
+              float dk[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                dk[j] = h + j < jn ? __ldg(a.Din + (zp - a.Zout) + (h + j) * ld) : 0.f;
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (h + j < jn) {
+                  const float f = tt[j] - dk[j] * inv_beta;
+                  const float e = zn[j] - f, ch = zn[j] - zz[j];
+                  s1 = fmaf(e, e, s1);
+                  s2 = fmaf(ch, ch, s2);
+                  s3 = fmaf(zn[j], zn[j], s3);
+                }
+            }
+            if (jn == GC) {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) __stcs(zp + (h + j) * ld, zn[j]);
+              if constexpr (WD) {
+                float* dp = a.Dout + (zp - a.Zout);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) dp[(h + j) * ld] = beta * (tt[j] - zn[j]);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (h + j < jn) {
+                  zp[(h + j) * ld] = zn[j];
+                  if constexpr (WD) a.Dout[(zp - a.Zout) + (h + j) * ld] = beta * (tt[j] - zn[j]);
+                }
             }
           }
-          wh[j] = tf32_rna(w);
-          wl[j] = tf32_rna(w - wh[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < GC; ++j) w[j] = 0.f;
         }
-        tst16(tmem + lane_base + T_W + 64 * p + half * HC, wh);
-        tst16(tmem + lane_base + T_W + 64 * p + 32 + half * HC, wl);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&zempty[sz]);   // the staged rows are no longer read
+        // product 2 of chunk gg - 2 has completed (it read the w buffer about to be
+        // rewritten); its sums join the running u'
+        if (i >= 2) consume_u(gg - 2);
+#pragma unroll
+        for (int j = 0; j < GC; j += 8) {
+          float wh[8], wl[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            wh[k] = tf32_rna(w[j + k]);
+            wl[k] = tf32_rna(w[j + k] - wh[k]);
+          }
+          tst8(tmem + lane_base + L::T_W + 64 * p + grp * GC + j, wh);
+          tst8(tmem + lane_base + L::T_W + 64 * p + 32 + grp * GC + j, wl);
+        }
         tst_wait();
         fence_before();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&w_full[p]);
-          mbar_arrive(&empty[s]);
-        }
-        if (i > 0) consume_u(gg - 1);
+        if (lane == 0) mbar_arrive(&w_full[p]);
       }
-      consume_u(g + nchk - 1);
+      for (int j = (nchk > 2 ? nchk - 2 : 0); j < nchk; ++j) consume_u(g + j);
       // this segment's partial u' (zero for voxels past the grid or outside the object)
-      float* po = a.Pout + ((tile * a.maxseg + sidx) * (int64_t)RP) * TV;
+      float* po = a.Pout + ((tile * spc + sg) * (int64_t)RP) * TV;
 #pragma unroll
-      for (int i = 0; i < RH; ++i) po[(half * RH + i) * TV + v] = in ? uacc[i] : 0.f;
+      for (int i = 0; i < RQ; ++i) po[(grp * RQ + i) * TV + v] = in ? uacc[i] : 0.f;
       g += nchk;
       ++si;
-      u = tile * nch + cend;
     }
   }
   if (failed) atomicExch(a.err, (int)SSM_ETIMEOUT);
@@ -590,9 +709,9 @@ __global__ void split_basis_kernel(const float* __restrict__ V32, int Q, int RP,
   }
 }
 
-template <int RP, int NR, bool CHECK>
+template <int RP, int NR, bool CHECK, bool WD>
 ssm_status set_attr() {
-  return cudaFuncSetAttribute(lrtc_kernel<RP, NR, CHECK>,
+  return cudaFuncSetAttribute(lrtc_kernel<RP, NR, CHECK, WD>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               Lay<RP, NR>::bytes) == cudaSuccess
              ? SSM_OK
@@ -602,24 +721,31 @@ ssm_status set_attr() {
 template <int RP, int NR>
 ssm_status prepare_rn() {
   if constexpr (Lay<RP, NR>::valid) {
-    SSM_TRY((set_attr<RP, NR, false>()));
-    SSM_TRY((set_attr<RP, NR, true>()));
+    SSM_TRY((set_attr<RP, NR, false, false>()));
+    SSM_TRY((set_attr<RP, NR, false, true>()));
+    SSM_TRY((set_attr<RP, NR, true, false>()));
+    SSM_TRY((set_attr<RP, NR, true, true>()));
   }
   return SSM_OK;
 }
 
 template <int RP, int NR>
-ssm_status launch_rn(const LrtcMaps& maps, const LrtcArgs& args, bool check, int64_t grid,
-                     cudaStream_t s) {
+ssm_status launch_rn(const LrtcMaps& maps, const LrtcArgs& args, bool check, bool write_d,
+                     int64_t grid, cudaStream_t s) {
   if constexpr (!Lay<RP, NR>::valid) {
     set_error("tensor-core low-rank form: this rank does not fit on 3D grids (r <= 32)");
     return SSM_EUNSUPPORTED;
   } else {
     const size_t shm = Lay<RP, NR>::bytes;
-    if (check)
-      lrtc_kernel<RP, NR, true><<<(unsigned)grid, NT, shm, s>>>(maps, args);
+    const unsigned gr = (unsigned)grid;
+    if (check && write_d)
+      lrtc_kernel<RP, NR, true, true><<<gr, Epi<NR>::NT, shm, s>>>(maps, args);
+    else if (check)
+      lrtc_kernel<RP, NR, true, false><<<gr, Epi<NR>::NT, shm, s>>>(maps, args);
+    else if (write_d)
+      lrtc_kernel<RP, NR, false, true><<<gr, Epi<NR>::NT, shm, s>>>(maps, args);
     else
-      lrtc_kernel<RP, NR, false><<<(unsigned)grid, NT, shm, s>>>(maps, args);
+      lrtc_kernel<RP, NR, false, false><<<gr, Epi<NR>::NT, shm, s>>>(maps, args);
     SSM_LAUNCHED();
     return SSM_OK;
   }
@@ -627,6 +753,30 @@ ssm_status launch_rn(const LrtcMaps& maps, const LrtcArgs& args, bool check, int
 
 int grid_nr(const ssm_plan_s* pl) {
   return (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 && pl->g.zlink ? 2 : 0);
+}
+
+int64_t ntiles_of(const ssm_plan_s* pl) { return (pl->g.N + TV - 1) / TV; }
+int64_t chunks_of(const ssm_plan_s* pl) { return (pl->Q + QC - 1) / QC; }
+
+// Launch layout: the CTAs' budget G0 (one per SM per launch wave); with at least G0 tiles
+// every tile is one unit (its whole Q range) and the grid is the fewest CTAs that keep the
+// rounds of G tiles equal; with fewer tiles each tile is split into spc segments of chunks
+// so that all CTAs have work.
+void layout(const ssm_plan_s* pl, int64_t* grid, int* spc) {
+  const int64_t ntiles = ntiles_of(pl), nch = chunks_of(pl);
+  int64_t g0 = (int64_t)sm_count() * std::max(1, pl->waves);
+  if (const char* env = getenv("SSM_LRTC_GRID")) {   // launch-shape override for sweeps
+    const long v = atol(env);
+    if (v >= 1 && v <= 65536) g0 = v;
+  }
+  if (ntiles >= g0) {
+    const int64_t rounds = (ntiles + g0 - 1) / g0;
+    *spc = 1;
+    *grid = (ntiles + rounds - 1) / rounds;
+  } else {
+    *spc = (int)std::max<int64_t>(1, std::min(nch, g0 / ntiles));
+    *grid = ntiles * *spc;
+  }
 }
 
 }  // namespace
@@ -638,27 +788,19 @@ int lrtc_padded_rank(int r, bool three_d) {
   return 0;
 }
 
-int64_t lrtc_chunks(const ssm_plan_s* pl) { return (pl->Q + QC - 1) / QC; }
-
 int64_t lrtc_grid(const ssm_plan_s* pl) {
-  const int64_t ntiles = (pl->g.N + TV - 1) / TV;
-  const int64_t T = ntiles * lrtc_chunks(pl);
-  int64_t grid = (int64_t)sm_count() * std::max(1, pl->waves);
-  if (const char* env = getenv("SSM_LRTC_GRID")) {   // launch-shape override for sweeps
-    const long v = atol(env);
-    if (v >= 1 && v <= 65536) grid = v;
-  }
-  return std::max<int64_t>(1, std::min(grid, T));
-}
-
-int lrtc_maxseg(const ssm_plan_s* pl, int64_t grid) {
-  const int64_t ntiles = (pl->g.N + TV - 1) / TV;
-  return (int)((grid + ntiles - 1) / ntiles + 1);
+  int64_t grid;
+  int spc;
+  layout(pl, &grid, &spc);
+  return grid;
 }
 
 int64_t lrtc_partial_floats(const ssm_plan_s* pl, int64_t grid) {
-  const int64_t ntiles = (pl->g.N + TV - 1) / TV;
-  return ntiles * lrtc_maxseg(pl, grid) * (int64_t)pl->R * TV;
+  (void)grid;
+  int64_t g;
+  int spc;
+  layout(pl, &g, &spc);
+  return ntiles_of(pl) * spc * (int64_t)pl->R * TV;
 }
 
 // once per process and device: the kernels' shared-memory limits
@@ -695,7 +837,13 @@ ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, dou
   SSM_CUDA(encode_2d(&m.v2l, F32, 4, pl->V2l, Q, RP, Qs, QC, (unsigned)RP, SW));
   SSM_CUDA(encode_2d(&m.zc, F32, 4, pl->Z[cur], N, Q, ld, ZW, QC));
   SSM_CUDA(encode_2d(&m.zn, F32, 4, pl->Z[cur], N, Q, ld, NW, QC));
-  const int64_t grid = pl->lr_grid;
+  int64_t grid;
+  int spc;
+  layout(pl, &grid, &spc);
+  if (grid != pl->lr_grid) {
+    set_error("tensor-core low-rank form: launch layout changed since planning");
+    return SSM_ECUDA;
+  }
   LrtcArgs a;
   a.Zout = pl->Z[cur ^ 1];
   a.Dout = pl->Dl[cur ^ 1];
@@ -703,10 +851,10 @@ ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, dou
   a.S = pl->S;
   a.Pin = pl->U[cur];
   a.Pout = pl->U[cur ^ 1];
-  a.ntiles = (pl->g.N + TV - 1) / TV;
-  a.nch = (int)lrtc_chunks(pl);
-  a.T = a.ntiles * a.nch;
-  a.maxseg = lrtc_maxseg(pl, grid);
+  a.ntiles = ntiles_of(pl);
+  a.nch = (int)chunks_of(pl);
+  a.spc = spc;
+  a.kr = std::max(1, std::min((int)RP / 8, (pl->r + 7) / 8));
   a.coefA = pl->coefA;
   a.coefW = pl->coefW;
   a.partial = partial;
@@ -714,7 +862,6 @@ ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, dou
   a.err = pl->dev_err;
   a.g = pl->g;
   a.Q = pl->Q;
-  a.write_d = write_d ? 1 : 0;
   a.beta = (float)pl->p.beta;
   a.inv_beta = (float)(1.0 / pl->p.beta);
   a.xi = (float)pl->xi;
@@ -723,14 +870,14 @@ ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, dou
   *nparts = (int)grid;
   const int nr = grid_nr(pl);
   if (pl->R == 32) {
-    if (nr == 0) return launch_rn<32, 0>(m, a, check, grid, s);
-    if (nr == 2) return launch_rn<32, 2>(m, a, check, grid, s);
-    return launch_rn<32, 4>(m, a, check, grid, s);
+    if (nr == 0) return launch_rn<32, 0>(m, a, check, write_d, grid, s);
+    if (nr == 2) return launch_rn<32, 2>(m, a, check, write_d, grid, s);
+    return launch_rn<32, 4>(m, a, check, write_d, grid, s);
   }
   if (pl->R == 64) {
-    if (nr == 0) return launch_rn<64, 0>(m, a, check, grid, s);
-    if (nr == 2) return launch_rn<64, 2>(m, a, check, grid, s);
-    return launch_rn<64, 4>(m, a, check, grid, s);
+    if (nr == 0) return launch_rn<64, 0>(m, a, check, write_d, grid, s);
+    if (nr == 2) return launch_rn<64, 2>(m, a, check, write_d, grid, s);
+    return launch_rn<64, 4>(m, a, check, write_d, grid, s);
   }
   set_error("tensor-core low-rank form: unsupported padded rank");
   return SSM_EUNSUPPORTED;

@@ -60,6 +60,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
   return false;
 }
 
+// As mbar_try_wait, but a thread whose phase has not completed is suspended for up to
+// `suspend_ns` nanoseconds (it resumes as soon as the phase completes), so a waiting warp
+// does not take issue slots from working ones by polling.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned parity,
+                                                    unsigned suspend_ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(suspend_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait with suspension between polls: at most `limit` polls of up to 20 us each
+// (the default bounds the wait by about 1.3 s); false on timeout
+constexpr unsigned kSleepPollLimit = 1u << 16;
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, unsigned parity,
+                                                unsigned limit = kSleepPollLimit) {
+  for (unsigned i = 0; i < limit; ++i)
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+  return false;
+}
+
 // 2D tiled TMA load of one box into shared memory, completing on `bar`
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* bar) {
@@ -68,6 +96,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
+}
+
+// 2D tiled TMA prefetch of one box into L2 (no shared memory, no completion to wait for;
+// coordinates outside the tensor are ignored like a load's)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
 }
 
 __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
