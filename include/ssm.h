@@ -189,6 +189,19 @@ ssm_status ssm_solve(ssm_plan_t plan, const float* M_dev, int64_t ldm, float* F_
                      int64_t ldf, ssm_info* info, void* stream);
 
 /*
+ * Continue the iteration (checkpoint/resume within a plan, no counterpart in the paper):
+ * run max_iter more iterations from the state the plan's last completed ssm_solve /
+ * ssm_solve_resume left (z, d and the form's internal operands stay on the device
+ * between calls), with the same stopping rule, and write F = z. M must be the data of
+ * that solve (its projections are formed again). The iterates are exactly those of one
+ * solve running the iterations of both calls. info->iterations counts this call's
+ * iterations. SSM_EINVAL when the plan holds no state: before the first solve, after a
+ * failed one, or after ssm_plan_set_beta / ssm_plan_set_mask.
+ */
+ssm_status ssm_solve_resume(ssm_plan_t plan, const float* M_dev, int64_t ldm, float* F_dev,
+                            int64_t ldf, ssm_info* info, void* stream);
+
+/*
  * Same as ssm_solve with HOST buffers: M_host (P x N, ldm) is copied in, the solve
  * runs, F_host (Q x N, ldf) is copied out; returns after the copy-out completes.
  * Staging buffers are the plan's own (allocated at plan time).
@@ -282,6 +295,15 @@ ssm_status ssm_plan_set_graphs(ssm_plan_t plan, int enable);
  * (SSM_EUNSUPPORTED).
  */
 ssm_status ssm_plan_set_mask(ssm_plan_t plan, const uint8_t* mask_host, void* stream);
+
+/*
+ * Change the plan's stopping rule for later solves (max_iter >= 0, check_every >= 0,
+ * tolerances as in ssm_params); the factors, state and beta are kept, so a resumed solve
+ * (ssm_solve_resume) can run with a new budget. Host only; must not overlap a solve on
+ * the same plan.
+ */
+ssm_status ssm_plan_set_stopping(ssm_plan_t plan, int max_iter, int check_every,
+                                 double tol_primal, double tol_change);
 
 /*
  * Change the plan's beta without refactorising K (the spectral factors of Sec. III-D do

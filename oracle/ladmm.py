@@ -76,7 +76,7 @@ def dense_inverse(K, beta):
 
 def ladmm(K, M, dims, lam, beta, *, rank=None, dense=False, xi_p=None, iters=300,
           tol_primal=0.0, tol_change=0.0, check_every=10, pairs=2, rank_tol=5e-5,
-          return_history=False, mask=None):
+          return_history=False, mask=None, z0=None, d0=None):
     """Run Algorithm 2 (or its full-rank Eq. 26 variant with dense=True).
 
     rank: None -> the rank rule of Sec. III-E with `rank_tol`; int -> that r.
@@ -85,6 +85,9 @@ def ladmm(K, M, dims, lam, beta, *, rank=None, dense=False, xi_p=None, iters=300
     from a graph cannot raise its Laplacian's eigenvalues).
     mask: voxels inside the object (True); the problem is posed on them alone, with the
     pairs of the induced grid graph, and z, f, d are 0 outside.
+    z0, d0: the state (z^k, d^k) to continue from (Q x N each); None starts from zero as
+    Algorithm 2 does. f^{k+1} depends only on z^k and d^k, so continuing from the state
+    after k1 iterations for k2 more repeats a run of k1 + k2 iterations exactly.
     Returns a dict with z, f, d (Q x N), iterations run, r, xi_p and the check history.
     """
     if mask is not None:
@@ -92,10 +95,11 @@ def ladmm(K, M, dims, lam, beta, *, rank=None, dense=False, xi_p=None, iters=300
         if xi_p is None:
             xi_p = grid.xi_p_rule(lam, dims, pairs)
         sub_dtd = grid.dtd(dims, pairs, mask)[inside][:, inside]
+        sub = (lambda a: None if a is None else np.asarray(a, np.float64)[:, inside])
         res = _ladmm_core(K, np.asarray(M, np.float64)[:, inside], sub_dtd, lam, beta,
                           rank=rank, dense=dense, xi_p=xi_p, iters=iters,
                           tol_primal=tol_primal, tol_change=tol_change,
-                          check_every=check_every, rank_tol=rank_tol)
+                          check_every=check_every, rank_tol=rank_tol, z0=sub(z0), d0=sub(d0))
         for key in ("z", "f", "d"):
             full = np.zeros((res[key].shape[0], int(np.prod(dims))))
             full[:, inside] = res[key]
@@ -109,14 +113,14 @@ def ladmm(K, M, dims, lam, beta, *, rank=None, dense=False, xi_p=None, iters=300
     assert np.asarray(M).shape[0] == K_.shape[0] and int(np.prod(dims)) == np.asarray(M).shape[1]
     res = _ladmm_core(K, M, grid.dtd(dims, pairs), lam, beta, rank=rank, dense=dense,
                       xi_p=xi_p, iters=iters, tol_primal=tol_primal, tol_change=tol_change,
-                      check_every=check_every, rank_tol=rank_tol)
+                      check_every=check_every, rank_tol=rank_tol, z0=z0, d0=d0)
     if not return_history:
         res.pop("history", None)
     return res
 
 
 def _ladmm_core(K, M, DtD, lam, beta, *, rank, dense, xi_p, iters, tol_primal, tol_change,
-                check_every, rank_tol):
+                check_every, rank_tol, z0=None, d0=None):
     """Algorithm 2 on the voxels of M (columns) coupled by the given D^T D."""
     K = np.asarray(K, np.float64)
     M = np.asarray(M, np.float64)
@@ -137,8 +141,8 @@ def _ladmm_core(K, M, DtD, lam, beta, *, rank, dense, xi_p, iters, tol_primal, t
         G = Vr @ (sr[:, None] * (Ur.T @ M))
         W = lowrank_weights(sr, beta)
 
-    z = np.zeros((Q, N))
-    d = np.zeros((Q, N))
+    z = np.zeros((Q, N)) if z0 is None else np.array(z0, np.float64)
+    d = np.zeros((Q, N)) if d0 is None else np.array(d0, np.float64)
     f = np.zeros((Q, N))
     history = []
     k = 0

@@ -727,33 +727,43 @@ void fill_power_info(const ssm_plan_s* pl, ssm_info* info) {
   info->power_converged = pl->power_conv;
 }
 
+// resume: continue from the state the plan's last solve left (z, d, the tensor-core
+// operand w, the low-rank form's partial u) instead of the zero start
 ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int64_t ldf,
-                      ssm_info* info, cudaStream_t s) {
+                      ssm_info* info, cudaStream_t s, bool resume = false) {
   const ssm_params& p = pl->p;
   const int64_t ld = pl->g.ld;
   const size_t QN = (size_t)pl->Q * ld;
+  if (resume && !pl->has_state) {
+    set_error("nothing to resume: the plan has no iteration state (solve first)");
+    return SSM_EINVAL;
+  }
+  pl->has_state = false;   // set again when this solve completes
   // step 4: projections of the data on the singular vectors (FP64 accumulation)
   if (p.form == SSM_FORM_LOWRANK) {
     SSM_TRY(project_data(pl, M, ldm, pl->r, s));
     if (pl->R > pl->r)
       SSM_CUDA(cudaMemsetAsync(pl->S + (size_t)pl->r * ld, 0,
                                sizeof(float) * (size_t)(pl->R - pl->r) * ld, s));
-    SSM_CUDA(cudaMemsetAsync(
-        pl->U[0], 0, sizeof(float) * (size_t)lowrank_state_floats(pl, pl->lr_grid), s));
+    if (!resume)
+      SSM_CUDA(cudaMemsetAsync(
+          pl->U[0], 0, sizeof(float) * (size_t)lowrank_state_floats(pl, pl->lr_grid), s));
   } else {
     SSM_TRY(project_data(pl, M, ldm, pl->n, s));
     // h = M g = sum_i Gq_i c_i
     SSM_TRY(sgemm(pl->Q, (int)pl->g.N, pl->n, 1.f, pl->Gq32, pl->n, pl->C32, ld, 0.f, pl->H, ld,
                   s));
-    if (pl->Wf) SSM_CUDA(cudaMemsetAsync(pl->Wf, 0, sizeof(float) * QN, s));
-    if (pl->Whi[0]) {
+    if (pl->Wf && !resume) SSM_CUDA(cudaMemsetAsync(pl->Wf, 0, sizeof(float) * QN, s));
+    if (pl->Whi[0] && !resume) {
       const size_t WN = (size_t)pl->g.ld * pl->Qp;
       SSM_CUDA(cudaMemsetAsync(pl->Whi[0], 0, sizeof(__nv_bfloat16) * WN, s));
       SSM_CUDA(cudaMemsetAsync(pl->Wlo[0], 0, sizeof(__nv_bfloat16) * WN, s));
     }
   }
   // step 2: z = d = 0 (Algorithm 1: x = y = z = d_x = d_y = d_z = 0)
-  if (p.form == SSM_FORM_ADMM) {
+  if (resume) {
+    // the state stays as the last solve left it
+  } else if (p.form == SSM_FORM_ADMM) {
     const AdmmState& a = pl->adm;
     for (float* v : {a.x, a.y, a.z, a.dx, a.dy, a.dz})
       SSM_CUDA(cudaMemsetAsync(v, 0, sizeof(float) * QN, s));
@@ -773,13 +783,15 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
   }
 
   const bool use_tol = p.tol_primal > 0 || p.tol_change > 0;
-  int cur = 0, k = 0;
+  int cur = resume ? pl->cur_state : 0, k = 0;
   double rp = -1, rc = -1;
   ssm_status result = SSM_OK;
   bool converged = false;
-  // iteration j forms the residual sums when it ends on a test boundary or is the last
+  // iteration j forms the residual sums when it ends on a test boundary or is the last;
+  // "iteration max_iter" counts as a test, so the last iteration also stores d (the
+  // low-rank forms keep d only around tests), which a resumed solve's first test reads
   auto is_check = [&](int j) {
-    if (j >= p.max_iter) return false;
+    if (j >= p.max_iter) return j == p.max_iter;
     const bool at = p.check_every > 0 && ((j + 1) % p.check_every == 0);
     return (use_tol && at) || j + 1 == p.max_iter;
   };
@@ -813,6 +825,8 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
     }
   }
   if (use_tol && !converged) result = SSM_ENOTCONVERGED;
+  pl->cur_state = cur;
+  pl->has_state = true;
   // F = z (the feasible iterate; y for Algorithm 1)
   const float* Fsrc = p.form == SSM_FORM_ADMM ? pl->adm.y : pl->Z[cur];
   SSM_CUDA(cudaMemcpy2DAsync(F, sizeof(float) * ldf, Fsrc, sizeof(float) * ld,
@@ -946,6 +960,20 @@ ssm_status ssm_solve(ssm_plan_t plan, const float* M_dev, int64_t ldm, float* F_
   return solve_impl(plan, M_dev, ldm, F_dev, ldf, info, static_cast<cudaStream_t>(stream));
 }
 
+ssm_status ssm_solve_resume(ssm_plan_t plan, const float* M_dev, int64_t ldm, float* F_dev,
+                            int64_t ldf, ssm_info* info, void* stream) {
+  if (!plan || !M_dev || !F_dev) {
+    set_error("NULL plan or buffer");
+    return SSM_EINVAL;
+  }
+  if (ldm < plan->g.N || ldf < plan->g.N) {
+    set_error("leading dimension smaller than N");
+    return SSM_EINVAL;
+  }
+  SSM_CUDA(cudaSetDevice(plan->device));
+  return solve_impl(plan, M_dev, ldm, F_dev, ldf, info, static_cast<cudaStream_t>(stream), true);
+}
+
 ssm_status ssm_solve_host(ssm_plan_t plan, const float* M_host, int64_t ldm, float* F_host,
                           int64_t ldf, ssm_info* info, void* stream) {
   if (!plan || !M_host || !F_host) {
@@ -1064,6 +1092,7 @@ ssm_status ssm_plan_set_mask(ssm_plan_t plan, const uint8_t* mask_host, void* st
   }
   SSM_CUDA(cudaSetDevice(plan->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  plan->has_state = false;   // another problem: nothing to resume
   // captured graphs hold the old mask pointer (or none) in their kernel arguments
   for (GraphBlock& b : plan->graphs)
     if (b.exec) cudaGraphExecDestroy(b.exec);
@@ -1082,6 +1111,26 @@ ssm_status ssm_plan_set_mask(ssm_plan_t plan, const uint8_t* mask_host, void* st
   return SSM_OK;
 }
 
+ssm_status ssm_plan_set_stopping(ssm_plan_t plan, int max_iter, int check_every,
+                                 double tol_primal, double tol_change) {
+  if (!plan) {
+    set_error("NULL plan");
+    return SSM_EINVAL;
+  }
+  if (max_iter < 0 || check_every < 0 || !(tol_primal == tol_primal) ||
+      !(tol_change == tol_change)) {
+    set_error("max_iter and check_every must be >= 0, tolerances not NaN");
+    return SSM_EINVAL;
+  }
+  plan->p.max_iter = max_iter;
+  plan->p.check_every = check_every;
+  plan->p.tol_primal = tol_primal;
+  plan->p.tol_change = tol_change;
+  // captured iteration blocks stay valid: a block is keyed by its length, start parity
+  // and test pattern, none of which a kernel argument depends on
+  return SSM_OK;
+}
+
 ssm_status ssm_plan_set_beta(ssm_plan_t plan, double beta, void* stream) {
   if (!plan) {
     set_error("NULL plan");
@@ -1094,6 +1143,7 @@ ssm_status ssm_plan_set_beta(ssm_plan_t plan, double beta, void* stream) {
   SSM_CUDA(cudaSetDevice(plan->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   plan->p.beta = beta;
+  plan->has_state = false;   // another iteration: nothing to resume
   // captured graphs hold the old beta in their kernel arguments
   for (GraphBlock& b : plan->graphs)
     if (b.exec) cudaGraphExecDestroy(b.exec);

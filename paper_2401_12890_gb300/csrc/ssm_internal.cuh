@@ -189,6 +189,9 @@ struct ssm_plan_s {
   float* adm_D = nullptr;
   // voxels inside the object (N bytes, 1 = inside), nullptr = every voxel
   uint8_t* mask = nullptr;
+  // the iteration state left by the last completed solve (ssm_solve_resume continues it)
+  bool has_state = false;
+  int cur_state = 0;           // ping-pong half holding z^k (and w^k, partial u)
   // iteration blocks replayed as CUDA graphs (ssm_plan_set_graphs)
   bool use_graphs = false;
   std::vector<ssm::GraphBlock> graphs;

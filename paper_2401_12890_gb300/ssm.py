@@ -134,6 +134,9 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SsmParams), vp, ctypes.c_int, vp]
     lib.ssm_solve.argtypes = [vp, fp, i64, fp, i64, ctypes.POINTER(SsmInfo), vp]
     lib.ssm_solve_host.argtypes = [vp, fp, i64, fp, i64, ctypes.POINTER(SsmInfo), vp]
+    lib.ssm_solve_resume.argtypes = [vp, fp, i64, fp, i64, ctypes.POINTER(SsmInfo), vp]
+    lib.ssm_plan_set_stopping.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double]
     lib.ssm_objective.argtypes = [vp, fp, i64, fp, i64, ctypes.c_int, dp, vp]
     lib.ssm_plan_factors.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     lib.ssm_plan_info.argtypes = [vp, ctypes.POINTER(SsmInfo)]
@@ -173,6 +176,7 @@ def load_library(path: str = LIB_PATH):
     lib.ssm_last_error.restype = ctypes.c_char_p
     lib.ssm_launch_count.restype = ctypes.c_int64
     for name in ("ssm_default_params", "ssm_plan", "ssm_solve", "ssm_solve_host",
+                 "ssm_solve_resume", "ssm_plan_set_stopping",
                  "ssm_objective", "ssm_plan_factors", "ssm_plan_info", "ssm_destroy",
                  "ssm_profile_enable",
                  "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
@@ -341,6 +345,31 @@ class Plan:
         if st not in (SSM_OK, SSM_ENOTCONVERGED):
             raise SsmError(st, "ssm_solve")
         return out, info.as_dict()
+
+    def resume(self, M, out=None, stream=None):
+        """Continue from the state the last solve left for max_iter more iterations
+        (ssm_solve_resume). Returns (F, info) like solve()."""
+        import torch
+        assert M.is_cuda and M.dtype == torch.float32 and M.dim() == 2 and M.stride(1) == 1
+        if out is None:
+            out = torch.empty((self.Q, self.N), dtype=torch.float32, device=M.device)
+        info = SsmInfo()
+        st = load_library().ssm_solve_resume(self._h, ctypes.c_void_p(M.data_ptr()), M.stride(0),
+                                             ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                                             ctypes.byref(info), _stream_handle(stream))
+        if st not in (SSM_OK, SSM_ENOTCONVERGED):
+            raise SsmError(st, "ssm_solve_resume")
+        return out, info.as_dict()
+
+    def set_max_iter(self, max_iter):
+        """The iteration budget of later solves (the plan's other parameters stay)."""
+        self.params.max_iter = int(max_iter)
+        st = load_library().ssm_plan_set_stopping(self._h, int(max_iter),
+                                                  int(self.params.check_every),
+                                                  float(self.params.tol_primal),
+                                                  float(self.params.tol_change))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_plan_set_stopping")
 
     def solve_async(self, M, out, stream=None):
         """As solve() without the info read-back (no host synchronisation unless a

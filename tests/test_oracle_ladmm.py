@@ -173,3 +173,15 @@ def test_stopping_rule_stops_on_check_boundary():
     # with no tolerance the budget is spent
     out = L.ladmm(K, M, (3, 2), 0.1, 1.0, iters=33, check_every=7)
     assert out["iters"] == 33
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_continuing_from_a_state_repeats_the_longer_run(dense):
+    """Algorithm 2's state is (z, d): k1 iterations, then k2 more from (z, d), are the
+    k1 + k2 iterations of one run, bit for bit."""
+    K, M, _ = synth.random_problem(9, 14, (6, 5), seed=4, snr=30.0)
+    kw = dict(rank=5, dense=dense, check_every=0)
+    full = L.ladmm(K, M, (6, 5), 0.2, 0.7, iters=25, **kw)
+    first = L.ladmm(K, M, (6, 5), 0.2, 0.7, iters=10, **kw)
+    rest = L.ladmm(K, M, (6, 5), 0.2, 0.7, iters=15, z0=first["z"], d0=first["d"], **kw)
+    assert np.array_equal(rest["z"], full["z"]) and np.array_equal(rest["d"], full["d"])
