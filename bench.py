@@ -698,7 +698,7 @@ def cpu_baseline_and_errors(K, M, w, Md, F, make_plan, forms):
 # serving: Poisson-arriving solves of mixed shapes through the continuous-batching server
 # --------------------------------------------------------------------------------------
 SERVE_SHAPES = ["dr2d_tiny", "dr2d_slice", "rr3d_t1t2"]
-SERVE_FORMS = [("dense", "bf16x3"), ("lowrank", "fp32")]
+SERVE_FORMS = [("lowrank", "tf32x3"), ("dense", "bf16x3")]
 SERVE_SEED = 46
 
 
@@ -802,7 +802,7 @@ def bench_serving(args):
             "hbm_budget_gb": st["budget"] / 1e9,
             "launch": "stream priority by footprint class (<= 64 MiB highest, one level per "
                       "factor 4 above); above the first class, persistent kernels in 8 "
-                      "launch waves",
+                      "launch waves; one of the 4 workers reserved for the first class",
         }
         torch.cuda.empty_cache()
     return out
@@ -829,7 +829,7 @@ def bench_batching():
     out = {"slices": BATCH_SLICES, "slice": f"{w.dims[0]}x{w.dims[1]}, P={w.P}, Q={w.Q}",
            "iterations": w.iters, "unit": METRIC, "forms": {}}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for form, prec in (("lowrank", "fp32"), ("dense", "bf16x3")):
+    for form, prec in (("lowrank", "tf32x3"), ("lowrank", "fp32"), ("dense", "bf16x3")):
         kw = dict(form=form, precision=prec, max_iter=w.iters, check_every=0)
         one = ssm.Plan(K, w.dims, w.lam, w.beta, **kw)
         one.set_graphs(True)

@@ -384,7 +384,9 @@ ssm_status ssm_destroy(ssm_plan_t plan);
  * HBM-bound, so the footprint stands for the cost of an iteration): up to `small_bytes`
  * is class 0, each factor of 4 above is one class more, up to the device's number of
  * stream priorities, and a class-c request runs on a stream of the c-th highest
- * priority. Requests above class 0 have their plans made by ssm_plan_ex(...,
+ * priority. `reserved_small` workers take class-0 requests only, so a small request is
+ * admitted even while large ones hold every other worker. Requests above class 0 have
+ * their plans made by ssm_plan_ex(...,
  * large_waves), so smaller solves get SMs within a fraction of a larger solve's
  * kernel. With `cache_plans`, a finished solve's plan (factors and
  * state) stays resident; a later request with the same K, grid and plan parameters
@@ -413,6 +415,10 @@ typedef struct {
                               iterations. 0 = normal operation                      */
   int64_t small_bytes;     /* footprint bound of the highest-priority class         */
   int large_waves;         /* launch waves of the plans of larger requests, 1..64    */
+  int reserved_small;      /* workers that admit class-0 requests only (so a small
+                              request never queues behind large ones holding every
+                              worker); < 0 selects 1 when max_active >= 2; at most
+                              max_active - 1                                         */
 } ssm_server_config;
 
 typedef struct {
@@ -440,7 +446,8 @@ typedef struct {
 } ssm_server_stats;
 
 /* Defaults: device 0, 4 workers, 90 % of free memory, graphs on, plan cache on,
- * max_bypass 2 * max_active, normal operation, small_bytes 64 MiB, large_waves 8. */
+ * max_bypass 2 * max_active, normal operation, small_bytes 64 MiB, large_waves 8,
+ * one worker reserved for class-0 requests. */
 ssm_status ssm_server_default_config(ssm_server_config* c);
 
 /* Create a server (threads and streams start here). */

@@ -19,6 +19,11 @@
 // arriving during a large one is not held up for the large one's kernels (which would
 // otherwise keep every SM for milliseconds).
 //
+// Reserved workers: the first `reserved_small` workers admit class-0 requests only, so a
+// small request never waits for a worker behind large ones that hold all the others
+// (stream priorities and launch waves help only a request that is already running).
+// The other workers take any request, first come first served.
+//
 // Memory accounting: every plan (running or idle) has a reservation, its peak
 // footprint while planning and its persistent footprint afterwards. `held` sums the
 // reservations of live plans, `dying` those of evicted plans not yet freed. A worker
@@ -137,9 +142,12 @@ struct ssm_server_s {
 
   // choose a request to run (caller holds mu); fills the plan to use and the idle
   // plans to free first
-  bool try_admit(Request** out, Resident** res_out, std::vector<std::unique_ptr<Resident>>* evict) {
+  bool try_admit(int slot, Request** out, Resident** res_out,
+                 std::vector<std::unique_ptr<Resident>>* evict) {
+    const bool small_only = slot < cfg.reserved_small;
     for (size_t i = 0; i < pending.size(); ++i) {
       Request* q = pending[i];
+      if (small_only && q->level != 0) continue;   // a reserved worker: class 0 only
       Resident* match = nullptr;
       if (cfg.cache_plans)
         for (auto& r : residents)
@@ -194,11 +202,12 @@ struct ssm_server_s {
         }
         peak = std::max(peak, held);
         pending.erase(pending.begin() + (std::ptrdiff_t)i);
-        if (i > 0) ++pending.front()->bypassed;
+        // passing the head counts against it only when this worker could have taken it
+        if (i > 0 && (!small_only || pending.front()->level == 0)) ++pending.front()->bypassed;
         *out = q;
         return true;
       }
-      if (i == 0 && q->bypassed >= cfg.max_bypass) return false;
+      if (i == 0 && q->bypassed >= cfg.max_bypass) return false;   // the head waits for memory
     }
     return false;
   }
@@ -257,7 +266,9 @@ struct ssm_server_s {
       std::vector<std::unique_ptr<Resident>> evict;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv_work.wait(lk, [&] { return stop || (!pending.empty() && try_admit(&q, &res, &evict)); });
+        cv_work.wait(lk, [&] {
+          return stop || (!pending.empty() && try_admit(slot, &q, &res, &evict));
+        });
         if (!q) return;   // stop
         ++active;
         q->t_admit = Clock::now();
@@ -368,7 +379,9 @@ ssm_status submit(ssm_server_t s, const ssm_params* p, const double* K_host, con
     SSM_CUDA(cudaSetDevice(s->cfg.device));
   }
   ssm_status fs = plan_footprint(*p, true, 1, &persistent, &q->footprint);
-  const int nlev = sim ? 1 : (int)s->streams.size();
+  // the scheduler test mode has no streams: it ranks requests as a device with six
+  // priority levels would (GB300's count)
+  const int nlev = sim ? 6 : (int)s->streams.size();
   for (int64_t b = std::max<int64_t>(1, s->cfg.small_bytes); q->footprint > b && q->level < nlev - 1;
        b *= 4)
     ++q->level;
@@ -415,6 +428,7 @@ ssm_status ssm_server_default_config(ssm_server_config* c) {
   c->simulate_us = 0;
   c->small_bytes = (int64_t)1 << 26;
   c->large_waves = 8;
+  c->reserved_small = -1;
   return SSM_OK;
 }
 
@@ -435,6 +449,9 @@ ssm_status ssm_server_create(ssm_server_t* out, const ssm_server_config* c) {
   auto s = std::make_unique<ssm_server_s>();
   s->cfg = *c;
   if (s->cfg.max_bypass < 0) s->cfg.max_bypass = 2 * c->max_active;
+  // one worker for class-0 requests when there are at least two; never all of them
+  if (s->cfg.reserved_small < 0) s->cfg.reserved_small = c->max_active >= 2 ? 1 : 0;
+  s->cfg.reserved_small = std::min(s->cfg.reserved_small, c->max_active - 1);
   const bool sim = c->simulate_us > 0;
   if (sim) {
     if (c->hbm_budget <= 0) {

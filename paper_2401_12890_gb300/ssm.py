@@ -60,6 +60,7 @@ class SsmServerConfig(ctypes.Structure):
         ("use_graphs", ctypes.c_int), ("cache_plans", ctypes.c_int),
         ("max_bypass", ctypes.c_int), ("simulate_us", ctypes.c_int64),
         ("small_bytes", ctypes.c_int64), ("large_waves", ctypes.c_int),
+        ("reserved_small", ctypes.c_int),
     ]
 
 
@@ -463,7 +464,7 @@ class Server:
 
     def __init__(self, *, device=0, max_active=4, hbm_budget=0, use_graphs=True,
                  cache_plans=True, max_bypass=-1, simulate_us=0, small_bytes=None,
-                 large_waves=None):
+                 large_waves=None, reserved_small=None):
         lib = load_library()
         c = SsmServerConfig()
         lib.ssm_server_default_config(ctypes.byref(c))
@@ -474,6 +475,8 @@ class Server:
             c.small_bytes = int(small_bytes)
         if large_waves is not None:
             c.large_waves = int(large_waves)
+        if reserved_small is not None:
+            c.reserved_small = int(reserved_small)
         self._h = ctypes.c_void_p()
         st = lib.ssm_server_create(ctypes.byref(self._h), ctypes.byref(c))
         if st != SSM_OK:

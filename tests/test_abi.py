@@ -37,7 +37,7 @@ def test_struct_layout_matches_header(lib, tmp_path):
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                    ' sizeof(ssm_params), sizeof(ssm_info), offsetof(ssm_params, tol_change),'
                    ' offsetof(ssm_info, plan_ms), sizeof(ssm_server_config),'
-                   ' offsetof(ssm_server_config, large_waves), sizeof(ssm_request_info),'
+                   ' offsetof(ssm_server_config, reserved_small), sizeof(ssm_request_info),'
                    ' offsetof(ssm_request_info, plan_reused), sizeof(ssm_server_stats),'
                    ' offsetof(ssm_server_stats, pending), sizeof(ssm_launch_info),'
                    ' offsetof(ssm_launch_info, tc_fused), offsetof(ssm_info, power_converged));'
@@ -49,7 +49,7 @@ def test_struct_layout_matches_header(lib, tmp_path):
                                            check=True).stdout.split()]
     assert vals == [ctypes.sizeof(ssm.SsmParams), ctypes.sizeof(ssm.SsmInfo),
                     ssm.SsmParams.tol_change.offset, ssm.SsmInfo.plan_ms.offset,
-                    ctypes.sizeof(ssm.SsmServerConfig), ssm.SsmServerConfig.large_waves.offset,
+                    ctypes.sizeof(ssm.SsmServerConfig), ssm.SsmServerConfig.reserved_small.offset,
                     ctypes.sizeof(ssm.SsmRequestInfo), ssm.SsmRequestInfo.plan_reused.offset,
                     ctypes.sizeof(ssm.SsmServerStats), ssm.SsmServerStats.pending.offset,
                     ctypes.sizeof(ssm.SsmLaunchInfo), ssm.SsmLaunchInfo.tc_fused.offset,

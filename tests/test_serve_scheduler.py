@@ -174,3 +174,38 @@ def test_invalid_server_config():
         ssm.Server(max_active=0, simulate_us=1, hbm_budget=1)
     with pytest.raises(ssm.SsmError):
         ssm.Server(max_active=1, simulate_us=1, hbm_budget=0)
+
+
+@pytest.mark.parametrize("reserved", [1, 0])
+def test_reserved_worker_admits_small_requests_past_large_ones(reserved):
+    """With a worker reserved for class-0 requests, a small request arriving while large
+    ones hold (or wait for) the other workers is admitted at once; without it, it waits
+    for a large one to finish."""
+    big, small = footprints()
+    with ssm.Server(max_active=2, hbm_budget=1 << 40, simulate_us=TICK_US, cache_plans=False,
+                    small_bytes=2 * small, reserved_small=reserved) as srv:
+        a = srv.submit(*problem(*BIG[:2], BIG[2], 1), BIG[2], 0.01, 1.0, max_iter=40)
+        time.sleep(0.02)
+        b = srv.submit(*problem(*BIG[:2], BIG[2], 2), BIG[2], 0.01, 1.0, max_iter=40)
+        time.sleep(0.02)
+        c = srv.submit(*problem(*SMALL[:2], SMALL[2], 3), SMALL[2], 0.01, 1.0, max_iter=2)
+        ia, ib, ic = (srv.wait(t)[1] for t in (a, b, c))
+    if reserved:
+        # B waits for A's worker; C takes the reserved one right away
+        assert (ia["order"], ic["order"], ib["order"]) == (0, 1, 2)
+        assert ic["queue_ms"] < 10 * TICK_US * 1e-3
+        assert ic["slot"] == 0 and ia["slot"] != 0 and ib["slot"] != 0
+    else:
+        assert (ia["order"], ib["order"], ic["order"]) == (0, 1, 2)
+        # A (40 ticks) started 20 ticks before C arrived
+        assert ic["queue_ms"] > 10 * TICK_US * 1e-3
+
+
+def test_reserved_workers_never_take_every_worker():
+    """reserved_small is capped at max_active - 1: large requests still run."""
+    big, small = footprints()
+    with ssm.Server(max_active=2, hbm_budget=1 << 40, simulate_us=TICK_US, cache_plans=False,
+                    small_bytes=2 * small, reserved_small=5) as srv:
+        info = srv.wait(srv.submit(*problem(*BIG[:2], BIG[2], 1), BIG[2], 0.01, 1.0,
+                                   max_iter=2))[1]
+    assert info["status"] == ssm.SSM_OK and info["slot"] == 1
