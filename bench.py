@@ -347,7 +347,10 @@ def bench_ours(args):
         return lambda Fz: plan.objective(Md, Fz, use_full_k=True)
 
     ttt = {}
-    for form, prec in available:
+    explicit = None if args.form == "auto" else tuple(args.form.split("_"))
+    # --quick with a named form: that form alone (profiling runs)
+    ttt_forms = [explicit] if (args.quick and explicit in available) else available
+    for form, prec in ttt_forms:
         key = form_key(form, prec)
         rec = {}
         # time to tolerance by the paper's residual rule: fresh solves to ||z-f|| and
@@ -394,8 +397,7 @@ def bench_ours(args):
         else:
             head = ("lowrank", "tf32x3") if ("lowrank", "tf32x3") in available else available[0]
     else:
-        f, p = args.form.split("_")
-        head = (f, p)
+        head = explicit
     forms_to_run = [head] if args.quick else [head] + [fp for fp in available if fp != head]
     headline = None
     for form, prec in forms_to_run:
@@ -497,6 +499,7 @@ def bench_ours(args):
     workloads = None
     if dist.world == 1 and not args.quick and not args.no_workloads:
         workloads = bench_workloads(args)
+        workloads["mrf_b1"] = bench_multidict()
 
     if dist.rank == 0:
         hl = headline
@@ -652,6 +655,117 @@ def bench_workloads(args):
         del Md, F
         torch.cuda.empty_cache()
     return out
+
+
+def patch_z_multi(Ks, labels, M, dims, lam, beta, xi, n_iter, centre):
+    """As patch_z for spatially varying dictionaries (oracle.multidict), with only the
+    patch's dictionaries (relabelling them changes nothing)."""
+    from oracle import multidict as MD
+    lo = [max(0, c - n_iter) for c in centre]
+    hi = [min(d, c + n_iter + 1) for c, d in zip(centre, dims)]
+    pd = tuple(h - l for l, h in zip(lo, hi))
+    cols = []
+    for idx in np.ndindex(*reversed(pd)):
+        coord = list(reversed(idx))
+        flat, stride = 0, 1
+        for ax in range(len(dims)):
+            flat += (lo[ax] + coord[ax]) * stride
+            stride *= dims[ax]
+        cols.append(flat)
+    present, local = np.unique(labels[cols], return_inverse=True)
+    res = MD.ladmm_multi([Ks[c] for c in present], local, M[:, cols], pd, lam, beta, xi_p=xi,
+                         iters=n_iter, check_every=0)
+    loc, stride, flat, fstride = 0, 1, 0, 1
+    for ax in range(len(dims)):
+        loc += (centre[ax] - lo[ax]) * stride
+        stride *= pd[ax]
+        flat += centre[ax] * fstride
+        fstride *= dims[ax]
+    return res["z"][:, loc], flat
+
+
+def bench_multidict():
+    """The fingerprinting stand-in with a dictionary per B1 level (61 levels, 156 x 156,
+    P = 120, Q = 900): device time per iteration of the spatially varying dictionary path
+    (difference of two solve lengths, CUDA events), its kernel's roofline fraction, the
+    same grid with one dictionary for every voxel (the single-dictionary FP32 low-rank
+    kernel) for the cost of the per-voxel dictionaries, and the error at sampled voxels
+    against the FP64 oracle on their patches."""
+    import torch
+
+    from oracle import grid
+    from paper_2401_12890_gb300 import ssm, synth
+    pk = measured_peaks()
+    w = synth.B1_WORKLOAD
+    Ks, labels, M, _ = synth.make_b1_problem()
+    Md = torch.from_numpy(M).cuda()
+    F = torch.empty((w.Q, w.N), dtype=torch.float32, device="cuda")
+    rec = {"dims": list(w.dims), "P": w.P, "Q": w.Q, "N": w.N, "levels": len(Ks),
+           "labels": "a smooth B1 field quantised to the levels"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def per_iteration(plan, k1=20, k2=60):
+        times = {}
+        for k in (k1, k2):
+            plan.set_max_iter(k)
+            plan.solve_async(Md, F)
+            torch.cuda.synchronize()
+            e0.record()
+            plan.solve_async(Md, F)
+            e1.record()
+            torch.cuda.synchronize()
+            times[k] = e0.elapsed_time(e1)
+        return (times[k2] - times[k1]) / (k2 - k1)
+
+    t0 = time.perf_counter()
+    plan = ssm.MultiPlan(Ks, labels, w.dims, w.lam, w.beta, max_iter=20, check_every=0)
+    plan_s = time.perf_counter() - t0
+    per_it = per_iteration(plan)
+    plan.set_max_iter(60)
+    plan.profile(True)
+    plan.solve_async(Md, F)
+    kms, kl = plan.profile_read()
+    plan.profile(False)
+    info = plan.info()
+    launch = plan.launch_info()
+    r = info["rank"]
+    amount = 8.0 * w.Q * w.N + 12.0 * r * w.N + 4.0 * w.N
+    avg_s = kms / max(kl, 1) / 1e3
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    achieved = amount / avg_s / 1e9
+    n_err = 6
+    plan.set_max_iter(n_err)
+    Fz, _ = plan.solve(Md, F)
+    zg = Fz.cpu().numpy().astype(np.float64)
+    plan.close()
+    xi = grid.xi_p_rule(w.lam, w.dims)
+    errs = []
+    for centre in [(w.dims[0] // 2, w.dims[1] // 2), (0, 0), (w.dims[0] - 1, 17)]:
+        zr, flat = patch_z_multi(Ks, labels, M.astype(np.float64), w.dims, w.lam, w.beta, xi,
+                                 n_err, centre)
+        errs.append(float(np.linalg.norm(zg[:, flat] - zr) / max(np.linalg.norm(zr), 1e-300)))
+    rec["lowrank_fp32_multi"] = {
+        "us_per_iteration": 1e3 * per_it, "value": w.N * w.Q / (per_it / 1e3), "unit": METRIC,
+        "rank": r, "plan_s": plan_s, "segments_grid": launch.get("lowrank_grid"),
+        "roofline": {"bound": "hbm", "kernel": "multi_iter_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "main_kernel_ms_avg": kms / max(kl, 1),
+                     "algorithmic_per_launch": amount},
+        "err_vs_oracle": {"voxels": 3, "iterations": n_err, "max_rel_l2": max(errs),
+                          "oracle": "FP64 oracle.multidict on each voxel's patch"}}
+    # the same grid and data with one dictionary (the centre voxel's) for every voxel
+    c = int(labels[(w.dims[1] // 2) * w.dims[0] + w.dims[0] // 2])
+    one = ssm.Plan(Ks[c], w.dims, w.lam, w.beta, form="lowrank", precision="fp32",
+                   max_iter=20, check_every=0)
+    per_one = per_iteration(one)
+    one.close()
+    rec["lowrank_fp32_one_dictionary"] = {
+        "us_per_iteration": 1e3 * per_one, "value": w.N * w.Q / (per_one / 1e3),
+        "unit": METRIC, "note": "the centre voxel's dictionary for every voxel: the cost of "
+                                "one dictionary per voxel is the ratio of the two lines"}
+    del Md, F
+    torch.cuda.empty_cache()
+    return rec
 
 
 def cpu_baseline_and_errors(K, M, w, Md, F, make_plan, forms):

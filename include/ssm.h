@@ -174,6 +174,32 @@ ssm_status ssm_plan_batched(ssm_plan_t* out, const ssm_params* p, int64_t nbatch
                             const double* K_host, int device, void* stream, int launch_waves);
 
 /*
+ * Spatially varying dictionaries (Sec. IV-D: the fingerprinting experiment's dictionary
+ * per quantised B1 level): voxel n is modelled with dictionary c(n), so Eq. 7 becomes
+ *     min_{F >= 0} sum_n 1/2 ||m_n - K_{c(n)} f_n||^2 + lambda/2 ||D F||^2
+ * and Algorithm 2 runs unchanged but for the f-step, which takes the voxel's own
+ * dictionary's rank-r factors (Eq. 27, Eq. 28; each dictionary's rank by the rule of
+ * Sec. III-E with p->rank_tol, or p->rank for all). The z-step, the dual step, xi_p
+ * (Eq. 32) and the stopping rule are those of one dictionary.
+ *   p           : as for ssm_plan; form must be SSM_FORM_LOWRANK and precision SSM_FP32
+ *                 (else SSM_EUNSUPPORTED). P and Q are every dictionary's shape.
+ *   ndict       : number of dictionaries, 1..65536.
+ *   K_host      : ndict x P x Q doubles on the host, dictionary c at offset c P Q,
+ *                 each row-major P x Q; read during the call only.
+ *   labels_host : N int32 labels on the host (voxel order of M's columns), each in
+ *                 [0, ndict) (else SSM_EINVAL, nothing allocated); read during the call.
+ * Each dictionary's rank must be <= 32 (else SSM_EUNSUPPORTED). ssm_solve,
+ * ssm_solve_host, ssm_solve_resume, ssm_plan_set_stopping, graphs, profiling and
+ * ssm_plan_info apply (info->rank and sigma1 are the largest over the dictionaries,
+ * kk_norm the largest lambda_max(K_c^T K_c); hess_norm is not formed, 0). ssm_objective,
+ * ssm_plan_factors, ssm_plan_set_mask and ssm_plan_set_beta return SSM_EUNSUPPORTED.
+ * Planning synchronises `stream`.
+ */
+ssm_status ssm_plan_multi(ssm_plan_t* out, const ssm_params* p, int ndict,
+                          const double* K_host, const int32_t* labels_host, int device,
+                          void* stream);
+
+/*
  * Run the LADMM iteration (Algorithm 2, steps 4-12) on data M and write F = z.
  *   M_dev : P x N floats on the device, leading dimension ldm >= N; read only.
  *   F_dev : Q x N floats on the device, leading dimension ldf >= N; written.

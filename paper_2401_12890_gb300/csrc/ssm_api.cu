@@ -84,6 +84,7 @@ double dtd_norm_closed(const int64_t* dims, int ndim, int pairs) {
 
 // floats of one partial-u buffer of the low-rank forms
 int64_t lowrank_state_floats(const ssm_plan_s* pl, int64_t grid) {
+  if (pl->ndict > 0) return multi_state_floats(pl, pl->mseg);
   return pl->p.precision == SSM_TF32X3 ? lrtc_partial_floats(pl, grid)
                                        : lowrank_partial_floats(pl, grid);
 }
@@ -203,6 +204,8 @@ void release(ssm_plan_s* pl) {
   for (auto& tt : pl->adm_T)
     for (float*& v : tt) dfree(v);
   dfree(pl->mask);
+  dfree(pl->labels);
+  dfree(pl->B_multi);
   dfree(pl->C32);
   dfree(pl->S);
   dfree(pl->H);
@@ -223,14 +226,11 @@ void release(ssm_plan_s* pl) {
   delete pl;
 }
 
-ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
+// grid, xi_p (Eq. 32) and the stencil weight of a plan from its parameters
+void setup_grid(ssm_plan_s* pl) {
   const ssm_params& p = pl->p;
-  SSM_CUDA(cudaEventCreate(&pl->ev0));
-  SSM_CUDA(cudaEventCreate(&pl->ev1));
-  SSM_CUDA(cudaEventRecord(pl->ev0, s));
-  const int P = p.P, Q = p.Q;
-  pl->P = P;
-  pl->Q = Q;
+  pl->P = p.P;
+  pl->Q = p.Q;
   pl->g.nx = (int)p.dims[0];
   pl->g.ny = p.ndim >= 2 ? (int)p.dims[1] : 1;
   pl->g.nz = p.ndim >= 3 ? (int)p.dims[2] : 1;
@@ -240,6 +240,15 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   pl->dtd_norm = dtd_norm_closed(p.dims, pl->g.zlink ? p.ndim : 2, p.stencil_pairs);
   pl->xi = p.xi_p > 0.0 ? p.xi_p : 0.75 * p.lambda * pl->dtd_norm + 1e-10;  // Eq. 32
   pl->lam_s = p.lambda * (p.stencil_pairs == 2 ? 2.0 : 1.0);
+}
+
+ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
+  const ssm_params& p = pl->p;
+  SSM_CUDA(cudaEventCreate(&pl->ev0));
+  SSM_CUDA(cudaEventCreate(&pl->ev1));
+  SSM_CUDA(cudaEventRecord(pl->ev0, s));
+  const int P = p.P, Q = p.Q;
+  setup_grid(pl);
   pl->n = std::min(P, Q);
   pl->gram_side = P <= Q ? 0 : 1;
   const int n = pl->n;
@@ -439,6 +448,136 @@ ssm_status plan_impl(ssm_plan_s* pl, const double* K_host, cudaStream_t s) {
   return SSM_OK;
 }
 
+// A plan with one dictionary per voxel label (ssm_plan_multi). Each dictionary is
+// factorised by an ordinary plan on a one-voxel grid (FP64 Gram matrix, power
+// iteration, Jacobi, the rank rule), one at a time; its basis V_r, weights and scaled
+// left factors sigma_i u_i are copied out at the largest padded stride, then repacked
+// to the common padded rank R.
+ssm_status multi_plan_impl(ssm_plan_s* pl, int ndict, const double* K_host,
+                           const int32_t* labels_host, cudaStream_t s) {
+  const ssm_params& p = pl->p;
+  SSM_CUDA(cudaEventCreate(&pl->ev0));
+  SSM_CUDA(cudaEventCreate(&pl->ev1));
+  SSM_CUDA(cudaEventRecord(pl->ev0, s));
+  setup_grid(pl);
+  const int P = p.P, Q = p.Q;
+  const int RM = kMaxMultiRank;
+  pl->n = std::min(P, Q);
+  pl->ndict = ndict;
+  pl->ranks.assign(ndict, 0);
+  // staging at stride RM: [c][q][i], [c][i], [c][p][i]
+  float *Vs = nullptr, *As = nullptr, *Ws = nullptr;
+  double* Bs = nullptr;
+  auto free_staging = [&]() {
+    cudaFreeAsync(Vs, s);
+    cudaFreeAsync(As, s);
+    cudaFreeAsync(Ws, s);
+    cudaFreeAsync(Bs, s);
+  };
+  SSM_TRY(dalloc(&Vs, (size_t)ndict * Q * RM, s));
+  SSM_TRY(dalloc(&As, (size_t)ndict * RM, s));
+  SSM_TRY(dalloc(&Ws, (size_t)ndict * RM, s));
+  SSM_TRY(dalloc(&Bs, (size_t)ndict * P * RM, s));
+  ssm_params sp = p;
+  sp.ndim = 1;
+  sp.dims[0] = sp.dims[1] = sp.dims[2] = 1;
+  sp.xi_p = 0.0;
+  int rmax = 0;
+  for (int c = 0; c < ndict; ++c) {
+    ssm_plan_t sub = nullptr;
+    ssm_status st = plan_create(&sub, &sp, K_host + (size_t)c * P * Q, pl->device, s, 1);
+    if (st == SSM_OK && sub->r > RM) {
+      set_error("spatially varying dictionaries: each dictionary's rank must be <= 32");
+      st = SSM_EUNSUPPORTED;
+    }
+    if (st == SSM_OK) {
+      const int r = sub->r;
+      pl->ranks[c] = r;
+      rmax = std::max(rmax, r);
+      pl->sigma1 = std::max(pl->sigma1, sub->sigma1);
+      pl->kk_power = std::max(pl->kk_power, sub->kk_power);
+      pl->power_iters = std::max(pl->power_iters, sub->power_iters);
+      pl->power_conv = c == 0 ? sub->power_conv : std::min(pl->power_conv, sub->power_conv);
+      cudaError_t e = cudaMemsetAsync(Vs + (size_t)c * Q * RM, 0, sizeof(float) * Q * RM, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(Vs + (size_t)c * Q * RM, sizeof(float) * RM, sub->V32,
+                              sizeof(float) * sub->R, sizeof(float) * r, Q,
+                              cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(As + (size_t)c * RM, 0, sizeof(float) * RM, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(Ws + (size_t)c * RM, 0, sizeof(float) * RM, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(As + (size_t)c * RM, sub->coefA, sizeof(float) * r,
+                            cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(Ws + (size_t)c * RM, sub->coefW, sizeof(float) * r,
+                            cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) {
+        set_error(std::string("copying a dictionary's factors: ") + cudaGetErrorString(e));
+        st = SSM_ECUDA;
+      }
+      if (st == SSM_OK)
+        st = multi_gather_factors(sub->Bp64, sub->alpha64, P, sub->n, r, RM,
+                                  Bs + (size_t)c * P * RM, s);
+      // the copies read the sub-plan's buffers: finish them before it is freed
+      if (cudaStreamSynchronize(s) != cudaSuccess && st == SSM_OK) st = SSM_ECUDA;
+    }
+    if (sub) release(sub);
+    if (st != SSM_OK) {
+      free_staging();
+      return st;
+    }
+  }
+  pl->r = rmax;
+  pl->R = multi_padded_rank(rmax);
+  // the common padded rank: repack the staged factors at stride R
+  ssm_status st = SSM_OK;
+  auto repack = [&]() -> ssm_status {
+    const int R = pl->R;
+    SSM_TRY(palloc(pl, &pl->V32, (size_t)ndict * Q * R, s));
+    SSM_TRY(palloc(pl, &pl->coefA, (size_t)ndict * R, s));
+    SSM_TRY(palloc(pl, &pl->coefW, (size_t)ndict * R, s));
+    SSM_TRY(palloc(pl, &pl->B_multi, (size_t)ndict * P * R, s));
+    SSM_CUDA(cudaMemcpy2DAsync(pl->V32, sizeof(float) * R, Vs, sizeof(float) * RM,
+                               sizeof(float) * R, (size_t)ndict * Q, cudaMemcpyDeviceToDevice, s));
+    SSM_CUDA(cudaMemcpy2DAsync(pl->coefA, sizeof(float) * R, As, sizeof(float) * RM,
+                               sizeof(float) * R, ndict, cudaMemcpyDeviceToDevice, s));
+    SSM_CUDA(cudaMemcpy2DAsync(pl->coefW, sizeof(float) * R, Ws, sizeof(float) * RM,
+                               sizeof(float) * R, ndict, cudaMemcpyDeviceToDevice, s));
+    SSM_CUDA(cudaMemcpy2DAsync(pl->B_multi, sizeof(double) * R, Bs, sizeof(double) * RM,
+                               sizeof(double) * R, (size_t)ndict * P, cudaMemcpyDeviceToDevice,
+                               s));
+    return SSM_OK;
+  };
+  st = repack();
+  free_staging();
+  if (st != SSM_OK) return st;
+
+  SSM_TRY(palloc(pl, &pl->labels, (size_t)pl->g.N, s));
+  SSM_CUDA(cudaMemcpyAsync(pl->labels, labels_host, sizeof(int32_t) * pl->g.N,
+                           cudaMemcpyHostToDevice, s));
+  SSM_TRY(palloc(pl, &pl->dev_err, 1, s));
+  SSM_CUDA(cudaMemsetAsync(pl->dev_err, 0, sizeof(int), s));
+  const size_t QN = (size_t)Q * pl->g.ld;
+  for (int i = 0; i < 2; ++i) {
+    SSM_TRY(palloc(pl, &pl->Z[i], QN, s));
+    SSM_TRY(palloc(pl, &pl->Dl[i], QN, s));
+  }
+  SSM_TRY(palloc(pl, &pl->S, (size_t)pl->R * pl->g.ld, s));
+  pl->mseg = multi_segments(pl);
+  pl->lr_grid = multi_grid(pl);
+  const size_t pf = (size_t)multi_state_floats(pl, pl->mseg);
+  for (int i = 0; i < 2; ++i) SSM_TRY(palloc(pl, &pl->U[i], pf, s));
+  const int maxparts = (int)std::max<int64_t>(pl->lr_grid, (pl->g.N + 255) / 256);
+  pl->red_cap = maxparts;
+  SSM_TRY(palloc(pl, &pl->red, (size_t)maxparts * 4, s));
+  SSM_TRY(palloc(pl, &pl->red_out, 8, s));
+  SSM_CUDA(cudaMallocHost(&pl->red_host, 8 * sizeof(double)));
+  SSM_CUDA(cudaEventRecord(pl->ev1, s));
+  SSM_CUDA(cudaEventSynchronize(pl->ev1));
+  SSM_CUDA(cudaEventElapsedTime(&pl->plan_ms, pl->ev0, pl->ev1));
+  return SSM_OK;
+}
+
 // Device bytes a plan for `p` takes, following plan_impl allocation by allocation:
 // `persistent` = what the plan holds between calls (with the staging buffers of
 // ssm_solve_host when `staging`), `peak` = persistent plus planning's temporaries
@@ -619,6 +758,10 @@ ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, bool check_next, i
     return prof_mark(pl, false, s);
   }
   SSM_TRY(prof_mark(pl, true, s));
+  if (pl->ndict > 0) {
+    SSM_TRY(multi_iteration(pl, cur, check, check_next, pl->red, nparts, s));
+    return prof_mark(pl, false, s);
+  }
   if (p.form == SSM_FORM_LOWRANK) {
     if (p.precision == SSM_TF32X3)
       SSM_TRY(lrtc_iteration(pl, cur, check, check_next, pl->red, nparts, s));
@@ -740,7 +883,13 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
   }
   pl->has_state = false;   // set again when this solve completes
   // step 4: projections of the data on the singular vectors (FP64 accumulation)
-  if (p.form == SSM_FORM_LOWRANK) {
+  if (pl->ndict > 0) {
+    // each voxel's projections on its own dictionary's factors (zero past its rank)
+    SSM_TRY(multi_project(pl, M, ldm, s));
+    if (!resume)
+      SSM_CUDA(cudaMemsetAsync(
+          pl->U[0], 0, sizeof(float) * (size_t)lowrank_state_floats(pl, pl->lr_grid), s));
+  } else if (p.form == SSM_FORM_LOWRANK) {
     SSM_TRY(project_data(pl, M, ldm, pl->r, s));
     if (pl->R > pl->r)
       SSM_CUDA(cudaMemsetAsync(pl->S + (size_t)pl->r * ld, 0,
@@ -946,6 +1095,52 @@ ssm_status ssm_plan_batched(ssm_plan_t* out, const ssm_params* p, int64_t nbatch
                      false);
 }
 
+ssm_status ssm_plan_multi(ssm_plan_t* out, const ssm_params* p, int ndict,
+                          const double* K_host, const int32_t* labels_host, int device,
+                          void* stream) {
+  if (!out) {
+    set_error("out is NULL");
+    return SSM_EINVAL;
+  }
+  *out = nullptr;
+  SSM_TRY(validate(p));
+  if (!K_host || !labels_host) {
+    set_error("K_host or labels_host is NULL");
+    return SSM_EINVAL;
+  }
+  if (ndict < 1 || ndict > 65536) {
+    set_error("ndict must be in [1, 65536]");
+    return SSM_EINVAL;
+  }
+  if (p->form != SSM_FORM_LOWRANK || p->precision != SSM_FP32) {
+    set_error("spatially varying dictionaries run the low-rank form in FP32");
+    return SSM_EUNSUPPORTED;
+  }
+  int64_t N = 1;
+  for (int d = 0; d < p->ndim; ++d) N *= p->dims[d];
+  for (int64_t i = 0; i < N; ++i)
+    if (labels_host[i] < 0 || labels_host[i] >= ndict) {
+      set_error("label " + std::to_string(labels_host[i]) + " of voxel " + std::to_string(i) +
+                " is outside [0, ndict)");
+      return SSM_EINVAL;
+    }
+  SSM_CUDA(cudaSetDevice(device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto* pl = new ssm_plan_s();
+  pl->p = *p;
+  pl->device = device;
+  pl->waves = 1;
+  pl->g.zlink = 1;
+  ssm_status st = multi_plan_impl(pl, ndict, K_host, labels_host, s);
+  if (st != SSM_OK) {
+    cudaStreamSynchronize(s);
+    release(pl);
+    return st;
+  }
+  *out = pl;
+  return SSM_OK;
+}
+
 ssm_status ssm_solve(ssm_plan_t plan, const float* M_dev, int64_t ldm, float* F_dev, int64_t ldf,
                      ssm_info* info, void* stream) {
   if (!plan || !M_dev || !F_dev) {
@@ -1005,6 +1200,10 @@ ssm_status ssm_objective(ssm_plan_t plan, const float* M_dev, int64_t ldm, const
     set_error("NULL argument");
     return SSM_EINVAL;
   }
+  if (plan->ndict > 0) {
+    set_error("the objective is not available for a plan with spatially varying dictionaries");
+    return SSM_EUNSUPPORTED;
+  }
   if (ldm < plan->g.N || ldf < plan->g.N) {
     set_error("leading dimension smaller than N");
     return SSM_EINVAL;
@@ -1035,6 +1234,10 @@ ssm_status ssm_plan_factors(ssm_plan_t plan, double* sigma_host, double* vr_host
   if (!plan) {
     set_error("NULL plan");
     return SSM_EINVAL;
+  }
+  if (plan->ndict > 0) {
+    set_error("ssm_plan_factors is not available for a plan with spatially varying dictionaries");
+    return SSM_EUNSUPPORTED;
   }
   if (sigma_host) std::memcpy(sigma_host, plan->sigma.data(), sizeof(double) * plan->n);
   if (rank_out) *rank_out = plan->r;
@@ -1086,6 +1289,10 @@ ssm_status ssm_plan_set_mask(ssm_plan_t plan, const uint8_t* mask_host, void* st
     set_error("NULL plan");
     return SSM_EINVAL;
   }
+  if (plan->ndict > 0) {
+    set_error("a mask is not available for a plan with spatially varying dictionaries");
+    return SSM_EUNSUPPORTED;
+  }
   if (plan->p.form == SSM_FORM_ADMM) {
     set_error("the ADMM form's z-step needs the whole box grid: masks are not supported");
     return SSM_EUNSUPPORTED;
@@ -1135,6 +1342,10 @@ ssm_status ssm_plan_set_beta(ssm_plan_t plan, double beta, void* stream) {
   if (!plan) {
     set_error("NULL plan");
     return SSM_EINVAL;
+  }
+  if (plan->ndict > 0) {
+    set_error("changing beta is not available for a plan with spatially varying dictionaries");
+    return SSM_EUNSUPPORTED;
   }
   if (!(beta > 0.0) || !std::isfinite(beta)) {
     set_error("beta must be > 0");

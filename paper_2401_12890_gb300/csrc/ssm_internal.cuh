@@ -192,6 +192,13 @@ struct ssm_plan_s {
   // the iteration state left by the last completed solve (ssm_solve_resume continues it)
   bool has_state = false;
   int cur_state = 0;           // ping-pong half holding z^k (and w^k, partial u)
+  // spatially varying dictionaries (ssm_plan_multi): ndict > 0. V32, coefA and coefW
+  // then hold every dictionary's factors ([c][q][i], [c][i]), padded to the common R
+  int ndict = 0;
+  int32_t* labels = nullptr;         // N dictionary labels
+  double* B_multi = nullptr;         // ndict x P x R: sigma_{c,i} u_{c,i} (S = B^T m per voxel)
+  int mseg = 1;                      // compartment segments per voxel tile
+  std::vector<int> ranks;            // r_c per dictionary
   // iteration blocks replayed as CUDA graphs (ssm_plan_set_graphs)
   bool use_graphs = false;
   std::vector<ssm::GraphBlock> graphs;
@@ -241,6 +248,18 @@ ssm_status lrtc_prepare();
 ssm_status lrtc_split_basis(ssm_plan_s* pl, cudaStream_t s);
 ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, double* partial,
                           int* nparts, cudaStream_t s);
+
+// spatially varying dictionaries (ssm_multidict.cu)
+constexpr int kMaxMultiRank = 32;
+int multi_padded_rank(int r);
+int multi_segments(const ssm_plan_s* pl);
+int64_t multi_grid(const ssm_plan_s* pl);
+int64_t multi_state_floats(const ssm_plan_s* pl, int nseg);
+ssm_status multi_gather_factors(const double* Bp, const double* alpha, int P, int n, int r, int R,
+                                double* out, cudaStream_t s);
+ssm_status multi_project(const ssm_plan_s* pl, const float* M, int64_t ldm, cudaStream_t s);
+ssm_status multi_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, double* partial,
+                           int* nparts, cudaStream_t s);
 
 // dense iteration and shared kernels (ssm_dense.cu)
 ssm_status sgemm(int M, int N, int K, float alpha, const float* A, int64_t lda,

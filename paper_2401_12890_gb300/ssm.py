@@ -151,6 +151,8 @@ def load_library(path: str = LIB_PATH):
                                 ctypes.c_int]
     lib.ssm_plan_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SsmParams), i64, vp,
                                      ctypes.c_int, vp, ctypes.c_int]
+    lib.ssm_plan_multi.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SsmParams), ctypes.c_int,
+                                   vp, vp, ctypes.c_int, vp]
     lib.ssm_server_submit_device.argtypes = [vp, ctypes.POINTER(SsmParams), vp, vp, i64, vp, i64,
                                              ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_plan_set_graphs.argtypes = [vp, ctypes.c_int]
@@ -183,7 +185,7 @@ def load_library(path: str = LIB_PATH):
                  "ssm_profile_read", "ssm_objective_noalloc", "ssm_plan_set_graphs",
                  "ssm_plan_ex", "ssm_server_submit_device", "ssm_plan_set_beta",
                  "ssm_tune_beta", "ssm_plan_launch_info", "ssm_plan_set_mask",
-                 "ssm_selftest_wait_timeout", "ssm_plan_batched",
+                 "ssm_selftest_wait_timeout", "ssm_plan_batched", "ssm_plan_multi",
                  "ssm_plan_footprint", "ssm_plan_device_bytes", "ssm_server_default_config",
                  "ssm_server_create", "ssm_server_submit", "ssm_server_poll", "ssm_server_wait",
                  "ssm_server_stats_read", "ssm_server_destroy"):
@@ -453,6 +455,40 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class MultiPlan(Plan):
+    """A planned solver with a dictionary per voxel label (ssm_plan_multi): Ks holds the
+    ndict dictionaries (each P x Q), labels the dictionary of every voxel (N ints in
+    voxel order). The low-rank form in FP32; solve/resume/set_max_iter/set_graphs/
+    profile/info as for Plan."""
+
+    def __init__(self, Ks, labels, dims, lam, beta, *, rank=0, rank_tol=5e-5, xi_p=0.0,
+                 stencil_pairs=2, max_iter=300, check_every=10, tol_primal=0.0,
+                 tol_change=0.0, device=0, stream=None):
+        lib = load_library()
+        Ks = np.ascontiguousarray(np.stack([np.asarray(K, np.float64) for K in Ks]))
+        ndict, P, Q = Ks.shape
+        lab = np.ascontiguousarray(np.asarray(labels).ravel(), dtype=np.int32)
+        dims = tuple(int(d) for d in dims)
+        assert lab.size == int(np.prod(dims)), "one label per voxel"
+        p = make_params(P, Q, dims, lam, beta, form="lowrank", precision="fp32", rank=rank,
+                        rank_tol=rank_tol, xi_p=xi_p, stencil_pairs=stencil_pairs,
+                        max_iter=max_iter, check_every=check_every, tol_primal=tol_primal,
+                        tol_change=tol_change)
+        self.params = p
+        self.dims = dims
+        self.P, self.Q = P, Q
+        self.N = lab.size
+        self.ndict = ndict
+        self.device = device
+        self._h = ctypes.c_void_p()
+        st = lib.ssm_plan_multi(ctypes.byref(self._h), ctypes.byref(p), int(ndict),
+                                Ks.ctypes.data_as(ctypes.c_void_p),
+                                lab.ctypes.data_as(ctypes.c_void_p), int(device),
+                                _stream_handle(stream))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_plan_multi")
 
 
 class Server:

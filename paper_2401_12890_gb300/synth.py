@@ -304,6 +304,28 @@ def b1_varying_problem(dims, levels, n_tp=60, t1_ms=None, t2_ms=None, seed=0, sn
     return Ks, labels, M, F
 
 
+# The fingerprinting experiment with a dictionary per B1 level (Sec. IV-D: 61 quantised
+# levels, one dictionary each, about 24000 voxels). Stand-in: the SPGR fingerprint
+# dictionary of the 2D fingerprinting workload's T1/T2 grid (30 x 30 atoms) at 120 time
+# points, at 61 B1 levels over [0.8, 1.2], on a 156 x 156 grid (24336 voxels) labelled
+# by a smooth B1 field. beta: the heuristic of Sec. III-E on the centre 3x3 patch with
+# the centre voxel's dictionary (tests/golden/make_golden.py records it).
+B1_LEVELS = 61
+B1_WORKLOAD = Workload("mrf_b1", (156, 156), 120, 900, 1e-2, 0.026549077590512404, 300,
+                       50.0, 48)
+
+
+def make_b1_problem(dims=None, levels=B1_LEVELS, seed=None):
+    """(Ks list of P x Q float64, labels int64 N, M float32 P x N, F_true float64) of the
+    spatially varying dictionary workload."""
+    w = B1_WORKLOAD
+    dims = tuple(dims) if dims is not None else w.dims
+    Ks, labels, M, F = b1_varying_problem(
+        dims, levels, n_tp=w.P, t1_ms=np.geomspace(200, 4000, 30),
+        t2_ms=np.geomspace(10, 300, 30), seed=w.seed if seed is None else seed, snr=w.snr)
+    return Ks, labels, M.astype(np.float32), F
+
+
 def grid_dims_for_n(n: int):
     """A 1D grid of n voxels (n x 1)."""
     return (int(n), 1)
@@ -316,7 +338,8 @@ def workload_summary(name):
 
 
 __all__ = [
-    "WORKLOADS", "Workload", "make_problem", "dictionary_for", "random_problem",
+    "WORKLOADS", "Workload", "make_problem", "B1_WORKLOAD", "B1_LEVELS", "make_b1_problem",
+    "dictionary_for", "random_problem",
     "diffusion_relaxation_dictionary", "inversion_recovery_dictionary",
     "spgr_fingerprint_dictionary", "spectral_peaks", "ground_truth_factors",
     "workload_summary", "grid_dims_for_n",

@@ -53,6 +53,7 @@ def test_grid_override_and_voxel_order():
 
 def test_workload_beta_matches_golden_record():
     g = json.load(open(os.path.join(HERE, "golden", "workloads.json")))
-    for name, w in synth.WORKLOADS.items():
+    for name, w in list(synth.WORKLOADS.items()) + [("mrf_b1", synth.B1_WORKLOAD)]:
         assert w.beta == pytest.approx(g[name]["beta"], rel=1e-12)
         assert w.P == g[name]["P"] and w.Q == g[name]["Q"]
+    assert g["mrf_b1"]["levels"] == synth.B1_LEVELS
