@@ -32,7 +32,9 @@
 // dealt round-robin to the CTAs; a segment is a contiguous run of a tile's chunks (one
 // segment per tile when there are at least as many tiles as CTAs, several otherwise).
 // CTAs running together therefore hold the same chunks of consecutive tiles, and the
-// neighbour rows each of them stages were just read by another: L2 hits. Each segment
+// neighbour rows each of them stages were just read by another: L2 hits. With between
+// half as many tiles as CTAs and as many, each tile is one main unit and one tail unit
+// instead, the tails going to the CTAs that would otherwise idle (see layout()). Each segment
 // writes its partial u' to its own slot; the next iteration sums a tile's slots in
 // segment order (fixed, hence deterministic). Warp roles:
 //   warp 0      TMA: per chunk, z with its x halo, the -+nx (-+nx*ny) neighbour rows and
@@ -139,6 +141,7 @@ struct LrtcArgs {
   int64_t ntiles;                   // voxel tiles
   int nch;                          // compartment chunks per tile
   int spc;                          // segments per tile (each a contiguous run of chunks)
+  int split;                        // > 0: main/tail layout, the chunk where tails start
   int kr;                           // K steps of 8 ranks holding the rank r (<= RP / 8)
   const float* __restrict__ coefA;  // RP
   const float* __restrict__ coefW;  // RP
@@ -301,6 +304,34 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
     c0 = (int)((int64_t)sg * nch / spc);
     c1 = (int)((int64_t)(sg + 1) * nch / spc);
   };
+  // the k-th unit of this CTA. Main/tail layout (a.split > 0, fewer tiles than CTAs but
+  // more than half as many): CTA j < ntiles owns chunks [0, split) of tile j; the other
+  // CTAs take the tails [split, nch) of tiles j - ntiles, j - ntiles + (G - ntiles), ...
+  // (concurrent tails are of consecutive tiles too). Otherwise units are dealt
+  // round-robin in segment-major order.
+  auto unit_at = [&](int k, int64_t& tile, int& c0, int& c1, int& sg) -> bool {
+    if (a.split > 0) {
+      const int64_t j = blockIdx.x, G = gridDim.x;
+      if (j < a.ntiles) {
+        if (k > 0) return false;
+        tile = j;
+        sg = 0;
+        c0 = 0;
+        c1 = a.split;
+        return true;
+      }
+      tile = j - a.ntiles + (int64_t)k * (G - a.ntiles);
+      if (tile >= a.ntiles) return false;
+      sg = 1;
+      c0 = a.split;
+      c1 = nch;
+      return true;
+    }
+    const int64_t u = blockIdx.x + (int64_t)k * gridDim.x;
+    if (u >= nunits) return false;
+    unit_of(u, tile, c0, c1, sg);
+    return true;
+  };
 
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
@@ -310,10 +341,9 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
       tma_prefetch_map(&maps.v1h);
       tma_prefetch_map(&maps.v2h);
       int g = 0;
-      for (int64_t u = blockIdx.x; u < nunits && !failed; u += gridDim.x) {
-        int64_t tile;
-        int c0, c1, sg;
-        unit_of(u, tile, c0, c1, sg);
+      int64_t tile;
+      int c0, c1, sg;
+      for (int k = 0; !failed && unit_at(k, tile, c0, c1, sg); ++k) {
         const int64_t n0 = tile * TV;
         // the tile's own z rows come from HBM: they are prefetched into L2 kPrefetch chunks
         // ahead of their staged loads, so that enough bytes are in flight per SM (the
@@ -389,10 +419,9 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
         commit(&vempty[gg % NSV]);    // the V stage is free once these complete
       };
       int g = 0, si = 0;
-      for (int64_t u = blockIdx.x; u < nunits && !failed; u += gridDim.x) {
-        int64_t tile;
-        int c0, c1, sg;
-        unit_of(u, tile, c0, c1, sg);
+      int64_t tile;
+      int c0, c1, sg;
+      for (int k = 0; !failed && unit_at(k, tile, c0, c1, sg); ++k) {
         const int nchk = c1 - c0;
         if (!mbar_wait_sleep(a_ready, si & 1)) {
           failed = true;
@@ -445,10 +474,9 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
     const float c3 = a.beta * a.inv_xb;              // weight of V a
     const float beta = a.beta, inv_beta = a.inv_beta;
     int g = 0, si = 0;
-    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-      int64_t tile;
-      int c0, c1, sg;
-      unit_of(u, tile, c0, c1, sg);
+    int64_t tile;
+    int c0, c1, sg;
+    for (int k = 0; unit_at(k, tile, c0, c1, sg); ++k) {
       const int nchk = c1 - c0;
       const int64_t n0 = tile * TV;
       const int64_t n = n0 + v;
@@ -758,21 +786,49 @@ int grid_nr(const ssm_plan_s* pl) {
 int64_t ntiles_of(const ssm_plan_s* pl) { return (pl->g.N + TV - 1) / TV; }
 int64_t chunks_of(const ssm_plan_s* pl) { return (pl->Q + QC - 1) / QC; }
 
-// Launch layout: the CTAs' budget G0 (one per SM per launch wave); with at least G0 tiles
-// every tile is one unit (its whole Q range) and the grid is the fewest CTAs that keep the
-// rounds of G tiles equal; with fewer tiles each tile is split into spc segments of chunks
-// so that all CTAs have work.
-void layout(const ssm_plan_s* pl, int64_t* grid, int* spc) {
+// Launch layout: the CTAs' budget G0 (one per SM per launch wave).
+//  - At least G0 tiles: every tile is one unit (its whole Q range) and the grid is the
+//    fewest CTAs that keep the rounds of G tiles equal.
+//  - Between G0/2 and G0 tiles (the 128x128 slice: 128 tiles, 152 SMs): one segment per
+//    tile would leave G0 - ntiles SMs idle, two would give some CTAs two whole-Q-halves
+//    of work; instead CTA j < ntiles takes chunks [0, split) of tile j and the spare
+//    CTAs take the tails, `split` chosen so that both kinds finish together (counting a
+//    unit's start as one chunk). On the slice: 126 us per launch at split 69 (150 CTAs)
+//    against 136 us with one segment per tile (128 CTAs); splits of 60 and 64 overload
+//    the tail CTAs (209 and 172 us).
+//  - Fewer tiles: each tile is split into spc equal segments so that all CTAs have work.
+void layout(const ssm_plan_s* pl, int64_t* grid, int* spc, int* split) {
   const int64_t ntiles = ntiles_of(pl), nch = chunks_of(pl);
   int64_t g0 = (int64_t)sm_count() * std::max(1, pl->waves);
   if (const char* env = getenv("SSM_LRTC_GRID")) {   // launch-shape override for sweeps
     const long v = atol(env);
     if (v >= 1 && v <= 65536) g0 = v;
   }
+  int64_t force_split = -1;
+  if (const char* env = getenv("SSM_LRTC_SPLIT")) {  // 0: no main/tail layout (sweeps)
+    const long v = atol(env);
+    if (v >= 0 && v < nch) force_split = v;
+  }
+  *split = 0;
   if (ntiles >= g0) {
     const int64_t rounds = (ntiles + g0 - 1) / g0;
     *spc = 1;
     *grid = (ntiles + rounds - 1) / rounds;
+  } else if (2 * ntiles > g0 && nch >= 4 && force_split != 0) {
+    const int64_t spare = g0 - ntiles;
+    const int64_t per = (ntiles + spare - 1) / spare;   // tails per spare CTA
+    int64_t best = 1, cost = INT64_MAX;
+    for (int64_t c = 1; c < nch; ++c) {
+      const int64_t t = std::max(c + 1, per * (nch - c + 1));
+      if (t < cost) {
+        cost = t;
+        best = c;
+      }
+    }
+    if (force_split > 0) best = force_split;
+    *split = (int)best;
+    *spc = 2;
+    *grid = ntiles + (ntiles + per - 1) / per;
   } else {
     *spc = (int)std::max<int64_t>(1, std::min(nch, g0 / ntiles));
     *grid = ntiles * *spc;
@@ -790,16 +846,16 @@ int lrtc_padded_rank(int r, bool three_d) {
 
 int64_t lrtc_grid(const ssm_plan_s* pl) {
   int64_t grid;
-  int spc;
-  layout(pl, &grid, &spc);
+  int spc, split;
+  layout(pl, &grid, &spc, &split);
   return grid;
 }
 
 int64_t lrtc_partial_floats(const ssm_plan_s* pl, int64_t grid) {
   (void)grid;
   int64_t g;
-  int spc;
-  layout(pl, &g, &spc);
+  int spc, split;
+  layout(pl, &g, &spc, &split);
   return ntiles_of(pl) * spc * (int64_t)pl->R * TV;
 }
 
@@ -838,8 +894,8 @@ ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, dou
   SSM_CUDA(encode_2d(&m.zc, F32, 4, pl->Z[cur], N, Q, ld, ZW, QC));
   SSM_CUDA(encode_2d(&m.zn, F32, 4, pl->Z[cur], N, Q, ld, NW, QC));
   int64_t grid;
-  int spc;
-  layout(pl, &grid, &spc);
+  int spc, split;
+  layout(pl, &grid, &spc, &split);
   if (grid != pl->lr_grid) {
     set_error("tensor-core low-rank form: launch layout changed since planning");
     return SSM_ECUDA;
@@ -854,6 +910,7 @@ ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, dou
   a.ntiles = ntiles_of(pl);
   a.nch = (int)chunks_of(pl);
   a.spc = spc;
+  a.split = split;
   a.kr = std::max(1, std::min((int)RP / 8, (pl->r + 7) / 8));
   a.coefA = pl->coefA;
   a.coefW = pl->coefW;
