@@ -147,18 +147,19 @@ def measured_peaks():
         return None
 
 
-def traffic_record(kernel_file, kernel_name):
+def traffic_record(kernel_file, kernel_name, workload=None):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is
     unchanged since the capture (profiles/traffic.json records its hash) and the capture
     was of the workload being run."""
+    workload = workload or WORKLOAD
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[
-            f"{kernel_name} @ {WORKLOAD}"]
+            f"{kernel_name} @ {workload}"]
     except (OSError, ValueError, KeyError):
         return None
     src = os.path.join(ROOT, "paper_2401_12890_gb300", "csrc", kernel_file)
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha") != h or rec.get("bench_workload", "dr2d_slice") != WORKLOAD:
+    if rec.get("source_sha") != h or rec.get("bench_workload", "dr2d_slice") != workload:
         return None
     return rec.get("dram_bytes_per_launch_full")
 
@@ -622,7 +623,7 @@ def bench_workloads(args):
             plan.profile(False)
             info = plan.info()
             launch = plan.launch_info()
-            _, _, bound, amount, unit, tkey = dominant_kernel(
+            _, kfile, bound, amount, unit, tkey = dominant_kernel(
                 form, prec, w.Q, w.N, info["rank"], int(launch.get("tc_fused", 0)))
             avg_s = kms / max(kl, 1) / 1e3
             if bound == "hbm":
@@ -647,7 +648,8 @@ def bench_workloads(args):
                 "value": w.N * w.Q / (per_it / 1e3), "unit": METRIC, "rank": info["rank"],
                 "roofline": {"bound": bound, "kernel": tkey, "achieved": achieved,
                              "peak": peak, "unit": unit, "frac": achieved / peak,
-                             "main_kernel_ms_avg": kms / max(kl, 1)},
+                             "main_kernel_ms_avg": kms / max(kl, 1),
+                             "traffic": traffic_record(kfile, tkey, name)},
                 "err_vs_oracle": {"voxel": list(centre), "iterations": n_err,
                                   "rel_l2": err, "oracle": "FP64 on the voxel's patch"}}
             torch.cuda.empty_cache()
@@ -747,10 +749,12 @@ def bench_multidict():
     rec["lowrank_fp32_multi"] = {
         "us_per_iteration": 1e3 * per_it, "value": w.N * w.Q / (per_it / 1e3), "unit": METRIC,
         "rank": r, "plan_s": plan_s, "segments_grid": launch.get("lowrank_grid"),
-        "roofline": {"bound": "hbm", "kernel": "multi_iter_kernel", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "table_iter_kernel", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "main_kernel_ms_avg": kms / max(kl, 1),
-                     "algorithmic_per_launch": amount},
+                     "algorithmic_per_launch": amount,
+                     "traffic": traffic_record("ssm_table.cu", "table_iter_kernel",
+                                               w.name)},
         "err_vs_oracle": {"voxels": 3, "iterations": n_err, "max_rel_l2": max(errs),
                           "oracle": "FP64 oracle.multidict on each voxel's patch"}}
     # the same grid and data with one dictionary (the centre voxel's) for every voxel

@@ -200,6 +200,47 @@ ssm_status ssm_plan_multi(ssm_plan_t* out, const ssm_params* p, int ndict,
                           void* stream);
 
 /*
+ * Groups: independent low-rank problems of differing N, P and Q solved together, one
+ * launch per iteration for all of them (the work-table kernel: a table of (problem,
+ * voxel tile, compartment segment) entries, one per block). For many small solves (the
+ * serving path's smallest requests) this replaces one launch per problem per iteration.
+ * No counterpart in the paper: each problem runs Algorithm 2 exactly as ssm_solve does,
+ * with its own stopping rule, and leaves the group when it stops.
+ *   plans : nplans plans on one device, each SSM_FORM_LOWRANK / SSM_FP32, rank <= 32,
+ *           one dictionary (not ssm_plan_multi), no mask (else SSM_EUNSUPPORTED). The
+ *           group borrows them: they must outlive it. It copies their factors (V_r, the
+ *           weights, sigma_i u_i) at creation, so a later ssm_plan_set_beta needs a new
+ *           group, and it runs in their state buffers (z, d), so a plan must not be
+ *           solved on its own while a group solve that holds it runs.
+ * A problem's iterates do not depend on the other problems of the group (nor on their
+ * ranks): a problem solved in any group gives the same bits. They are not the bits of
+ * ssm_solve (another kernel, another summation order), within rounding of them.
+ */
+typedef struct ssm_group_s* ssm_group_t;
+
+ssm_status ssm_group_create(ssm_group_t* out, int nplans, const ssm_plan_t* plans,
+                            void* stream);
+
+/*
+ * Solve every problem of the group. M_devs[i] (P_i x N_i, leading dimension ldms[i]) and
+ * F_devs[i] (Q_i x N_i, ldfs[i]) are device buffers; infos (nplans entries, may be NULL)
+ * receive each problem's status, iterations and residuals as ssm_solve's info. Each
+ * problem uses its plan's max_iter, check_every and tolerances. Returns SSM_OK when
+ * every problem ended SSM_OK, else the first error status among the problems (then
+ * SSM_ENOTCONVERGED if only some ran out of iterations); every F is written. Synchronises
+ * `stream` at each residual test.
+ */
+ssm_status ssm_group_solve(ssm_group_t group, const float* const* M_devs, const int64_t* ldms,
+                           float* const* F_devs, const int64_t* ldfs, ssm_info* infos,
+                           void* stream);
+
+/* Device bytes the group holds (its own buffers, not the plans'). */
+ssm_status ssm_group_device_bytes(ssm_group_t group, int64_t* bytes);
+
+/* Free the group (not its plans). NULL is accepted. */
+ssm_status ssm_group_destroy(ssm_group_t group);
+
+/*
  * Run the LADMM iteration (Algorithm 2, steps 4-12) on data M and write F = z.
  *   M_dev : P x N floats on the device, leading dimension ldm >= N; read only.
  *   F_dev : Q x N floats on the device, leading dimension ldf >= N; written.

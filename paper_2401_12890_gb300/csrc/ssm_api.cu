@@ -84,7 +84,7 @@ double dtd_norm_closed(const int64_t* dims, int ndim, int pairs) {
 
 // floats of one partial-u buffer of the low-rank forms
 int64_t lowrank_state_floats(const ssm_plan_s* pl, int64_t grid) {
-  if (pl->ndict > 0) return multi_state_floats(pl, pl->mseg);
+  if (pl->ndict > 0) return table_state_floats(pl->g.N, pl->mseg, pl->R);
   return pl->p.precision == SSM_TF32X3 ? lrtc_partial_floats(pl, grid)
                                        : lowrank_partial_floats(pl, grid);
 }
@@ -206,6 +206,8 @@ void release(ssm_plan_s* pl) {
   dfree(pl->mask);
   dfree(pl->labels);
   dfree(pl->B_multi);
+  dfree(pl->tprob);
+  dfree(pl->ttable);
   dfree(pl->C32);
   dfree(pl->S);
   dfree(pl->H);
@@ -461,7 +463,7 @@ ssm_status multi_plan_impl(ssm_plan_s* pl, int ndict, const double* K_host,
   SSM_CUDA(cudaEventRecord(pl->ev0, s));
   setup_grid(pl);
   const int P = p.P, Q = p.Q;
-  const int RM = kMaxMultiRank;
+  const int RM = kMaxTableRank;
   pl->n = std::min(P, Q);
   pl->ndict = ndict;
   pl->ranks.assign(ndict, 0);
@@ -516,7 +518,7 @@ ssm_status multi_plan_impl(ssm_plan_s* pl, int ndict, const double* K_host,
         st = SSM_ECUDA;
       }
       if (st == SSM_OK)
-        st = multi_gather_factors(sub->Bp64, sub->alpha64, P, sub->n, r, RM,
+        st = table_gather_factors(sub->Bp64, sub->alpha64, P, sub->n, r, RM,
                                   Bs + (size_t)c * P * RM, s);
       // the copies read the sub-plan's buffers: finish them before it is freed
       if (cudaStreamSynchronize(s) != cudaSuccess && st == SSM_OK) st = SSM_ECUDA;
@@ -528,7 +530,7 @@ ssm_status multi_plan_impl(ssm_plan_s* pl, int ndict, const double* K_host,
     }
   }
   pl->r = rmax;
-  pl->R = multi_padded_rank(rmax);
+  pl->R = table_padded_rank(rmax);
   // the common padded rank: repack the staged factors at stride R
   ssm_status st = SSM_OK;
   auto repack = [&]() -> ssm_status {
@@ -563,10 +565,40 @@ ssm_status multi_plan_impl(ssm_plan_s* pl, int ndict, const double* K_host,
     SSM_TRY(palloc(pl, &pl->Dl[i], QN, s));
   }
   SSM_TRY(palloc(pl, &pl->S, (size_t)pl->R * pl->g.ld, s));
-  pl->mseg = multi_segments(pl);
-  pl->lr_grid = multi_grid(pl);
-  const size_t pf = (size_t)multi_state_floats(pl, pl->mseg);
+  const int64_t ntiles = (pl->g.N + kTableTile - 1) / kTableTile;
+  pl->mseg = table_segments(ntiles, Q, pl->R);
+  const size_t pf = (size_t)table_state_floats(pl->g.N, pl->mseg, pl->R);
   for (int i = 0; i < 2; ++i) SSM_TRY(palloc(pl, &pl->U[i], pf, s));
+  // the iteration's problem descriptor and (tile, segment) table
+  std::vector<int4> entries;
+  table_entries(0, ntiles, pl->mseg, &entries);
+  pl->tblocks = (int64_t)entries.size();
+  pl->lr_grid = pl->tblocks;
+  TableProblem tp{};
+  for (int i = 0; i < 2; ++i) {
+    tp.Z[i] = pl->Z[i];
+    tp.D[i] = pl->Dl[i];
+    tp.U[i] = pl->U[i];
+  }
+  tp.S = pl->S;
+  tp.V = pl->V32;
+  tp.coefA = pl->coefA;
+  tp.coefW = pl->coefW;
+  tp.labels = pl->labels;
+  tp.g = pl->g;
+  tp.Q = Q;
+  tp.nseg = pl->mseg;
+  tp.beta = (float)p.beta;
+  tp.inv_beta = (float)(1.0 / p.beta);
+  tp.xi = (float)pl->xi;
+  tp.lam_s = (float)pl->lam_s;
+  tp.inv_xb = (float)(1.0 / (pl->xi + p.beta));
+  SSM_TRY(palloc(pl, &pl->tprob, 1, s));
+  SSM_TRY(palloc(pl, &pl->ttable, entries.size(), s));
+  SSM_CUDA(cudaMemcpyAsync(pl->tprob, &tp, sizeof(tp), cudaMemcpyHostToDevice, s));
+  SSM_CUDA(cudaMemcpyAsync(pl->ttable, entries.data(), sizeof(int4) * entries.size(),
+                           cudaMemcpyHostToDevice, s));
+  SSM_CUDA(cudaStreamSynchronize(s));   // the host copies are temporaries
   const int maxparts = (int)std::max<int64_t>(pl->lr_grid, (pl->g.N + 255) / 256);
   pl->red_cap = maxparts;
   SSM_TRY(palloc(pl, &pl->red, (size_t)maxparts * 4, s));
@@ -759,7 +791,9 @@ ssm_status one_iteration(ssm_plan_s* pl, int cur, bool check, bool check_next, i
   }
   SSM_TRY(prof_mark(pl, true, s));
   if (pl->ndict > 0) {
-    SSM_TRY(multi_iteration(pl, cur, check, check_next, pl->red, nparts, s));
+    SSM_TRY(table_iteration(pl->tprob, pl->ttable, pl->tblocks, pl->R, cur, check, check_next,
+                            pl->red, s));
+    *nparts = (int)pl->tblocks;
     return prof_mark(pl, false, s);
   }
   if (p.form == SSM_FORM_LOWRANK) {
@@ -885,7 +919,8 @@ ssm_status solve_impl(ssm_plan_s* pl, const float* M, int64_t ldm, float* F, int
   // step 4: projections of the data on the singular vectors (FP64 accumulation)
   if (pl->ndict > 0) {
     // each voxel's projections on its own dictionary's factors (zero past its rank)
-    SSM_TRY(multi_project(pl, M, ldm, s));
+    SSM_TRY(table_project(pl->B_multi, pl->P, pl->R, pl->labels, M, ldm, pl->g.N, pl->S,
+                          pl->g.ld, s));
     if (!resume)
       SSM_CUDA(cudaMemsetAsync(
           pl->U[0], 0, sizeof(float) * (size_t)lowrank_state_floats(pl, pl->lr_grid), s));

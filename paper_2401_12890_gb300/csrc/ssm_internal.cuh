@@ -87,6 +87,25 @@ struct DenseStep {
 // the largest padded rank the fused low-rank kernel is instantiated for
 constexpr int kMaxRank = 64;
 
+// One problem of the work-table iteration (ssm_table.cu): the low-rank d-free recurrence
+// on its own grid, with its own basis and state. The iteration kernel reads a table of
+// (problem, voxel tile, compartment segment) entries, one per block, so one launch can
+// run the iterations of several problems of differing N, P, Q.
+struct TableProblem {
+  float* Z[2];                      // z ping-pong (Q x ld)
+  float* D[2];                      // d ping-pong (Q x ld; read/written around tests)
+  float* U[2];                      // partial u per (tile, segment) [tile][seg][R][32]
+  const float* S;                   // R x ld: S_i = sigma_i u_i^T m per voxel
+  const float* V;                   // ndict x Q x R  [c][q][i]
+  const float* coefA;               // ndict x R: 1/(beta + sigma^2)
+  const float* coefW;               // ndict x R: sigma^2/(beta^2 + beta sigma^2)
+  const int32_t* labels;            // dictionary of each voxel (nullptr: dictionary 0)
+  Grid g;
+  int Q;
+  int nseg;                         // compartment segments per tile
+  float beta, inv_beta, xi, lam_s, inv_xb;
+};
+
 // the device state of Algorithm 1 (map-major Q x ld arrays)
 struct AdmmState {
   float *x, *y, *z, *dx, *dy, *dz;   // splits and duals
@@ -199,6 +218,9 @@ struct ssm_plan_s {
   double* B_multi = nullptr;         // ndict x P x R: sigma_{c,i} u_{c,i} (S = B^T m per voxel)
   int mseg = 1;                      // compartment segments per voxel tile
   std::vector<int> ranks;            // r_c per dictionary
+  ssm::TableProblem* tprob = nullptr;  // the iteration's problem descriptor (device)
+  int4* ttable = nullptr;            // its (problem, tile, segment) table (device)
+  int64_t tblocks = 0;               // entries of the table
   // iteration blocks replayed as CUDA graphs (ssm_plan_set_graphs)
   bool use_graphs = false;
   std::vector<ssm::GraphBlock> graphs;
@@ -249,17 +271,26 @@ ssm_status lrtc_split_basis(ssm_plan_s* pl, cudaStream_t s);
 ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, double* partial,
                           int* nparts, cudaStream_t s);
 
-// spatially varying dictionaries (ssm_multidict.cu)
-constexpr int kMaxMultiRank = 32;
-int multi_padded_rank(int r);
-int multi_segments(const ssm_plan_s* pl);
-int64_t multi_grid(const ssm_plan_s* pl);
-int64_t multi_state_floats(const ssm_plan_s* pl, int nseg);
-ssm_status multi_gather_factors(const double* Bp, const double* alpha, int P, int n, int r, int R,
+// work-table iteration (ssm_table.cu): a tile is 32 voxels; padded ranks 4, 8, .., 32
+constexpr int kTableTile = 32;
+constexpr int kMaxTableRank = 32;
+int table_padded_rank(int r);
+int table_blocks_per_sm(int R);
+// compartment segments per tile for a problem of ntiles tiles and Q compartments
+int table_segments(int64_t ntiles, int Q, int R);
+int64_t table_state_floats(int64_t N, int nseg, int R);   // one partial-u buffer
+// (problem, tile, segment) entries of one problem, segment-major, appended to `out`
+void table_entries(int problem, int64_t ntiles, int nseg, std::vector<int4>* out);
+// B [P][R] = alpha_i Bp[p][i] for i < r (sigma_i u_i), zero for r <= i < R
+ssm_status table_gather_factors(const double* Bp, const double* alpha, int P, int n, int r, int R,
                                 double* out, cudaStream_t s);
-ssm_status multi_project(const ssm_plan_s* pl, const float* M, int64_t ldm, cudaStream_t s);
-ssm_status multi_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, double* partial,
-                           int* nparts, cudaStream_t s);
+// S [R][ld] = B[c(n)]^T m_n per voxel (FP64 accumulation); labels nullptr: dictionary 0
+ssm_status table_project(const double* B, int P, int R, const int32_t* labels, const float* M,
+                         int64_t ldm, int64_t N, float* S, int64_t ld, cudaStream_t s);
+// one iteration of every problem of the table (blocks = entries); z^k in Z[cur]
+ssm_status table_iteration(const TableProblem* probs, const int4* table, int64_t nblocks, int R,
+                           int cur, bool check, bool write_d, double* partial, cudaStream_t s);
+
 
 // dense iteration and shared kernels (ssm_dense.cu)
 ssm_status sgemm(int M, int N, int K, float alpha, const float* A, int64_t lda,

@@ -153,6 +153,10 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.c_int, vp, ctypes.c_int]
     lib.ssm_plan_multi.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SsmParams), ctypes.c_int,
                                    vp, vp, ctypes.c_int, vp]
+    lib.ssm_group_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, vp]
+    lib.ssm_group_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(SsmInfo), vp]
+    lib.ssm_group_device_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.ssm_group_destroy.argtypes = [vp]
     lib.ssm_server_submit_device.argtypes = [vp, ctypes.POINTER(SsmParams), vp, vp, i64, vp, i64,
                                              ctypes.POINTER(ctypes.c_int64)]
     lib.ssm_plan_set_graphs.argtypes = [vp, ctypes.c_int]
@@ -186,6 +190,8 @@ def load_library(path: str = LIB_PATH):
                  "ssm_plan_ex", "ssm_server_submit_device", "ssm_plan_set_beta",
                  "ssm_tune_beta", "ssm_plan_launch_info", "ssm_plan_set_mask",
                  "ssm_selftest_wait_timeout", "ssm_plan_batched", "ssm_plan_multi",
+                 "ssm_group_create", "ssm_group_solve", "ssm_group_device_bytes",
+                 "ssm_group_destroy",
                  "ssm_plan_footprint", "ssm_plan_device_bytes", "ssm_server_default_config",
                  "ssm_server_create", "ssm_server_submit", "ssm_server_poll", "ssm_server_wait",
                  "ssm_server_stats_read", "ssm_server_destroy"):
@@ -489,6 +495,61 @@ class MultiPlan(Plan):
                                 _stream_handle(stream))
         if st != SSM_OK:
             raise SsmError(st, "ssm_plan_multi")
+
+
+class Group:
+    """Independent low-rank FP32 plans solved together, one launch per iteration for all
+    (ssm_group_*). The plans must stay open while the group is used."""
+
+    def __init__(self, plans, stream=None):
+        self.plans = list(plans)
+        n = len(self.plans)
+        arr = (ctypes.c_void_p * n)(*[p._h.value for p in self.plans])
+        self._h = ctypes.c_void_p()
+        st = load_library().ssm_group_create(ctypes.byref(self._h), n, arr,
+                                             _stream_handle(stream))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_group_create")
+
+    def solve(self, Ms, outs=None, stream=None):
+        """Ms: CUDA float32 tensors (P_i x N_i). Returns ([F_i], [info_i], status)."""
+        import torch
+        n = len(self.plans)
+        assert len(Ms) == n
+        if outs is None:
+            outs = [torch.empty((p.Q, p.N), dtype=torch.float32, device=M.device)
+                    for p, M in zip(self.plans, Ms)]
+        for p, M in zip(self.plans, Ms):
+            assert M.is_cuda and M.dtype == torch.float32 and M.stride(1) == 1
+            assert M.shape[0] == p.P and M.shape[1] == p.N
+        mp = (ctypes.c_void_p * n)(*[M.data_ptr() for M in Ms])
+        lm = (ctypes.c_int64 * n)(*[M.stride(0) for M in Ms])
+        fp = (ctypes.c_void_p * n)(*[F.data_ptr() for F in outs])
+        lf = (ctypes.c_int64 * n)(*[F.stride(0) for F in outs])
+        infos = (SsmInfo * n)()
+        st = load_library().ssm_group_solve(self._h, mp, lm, fp, lf, infos,
+                                            _stream_handle(stream))
+        if st not in (SSM_OK, SSM_ENOTCONVERGED):
+            raise SsmError(st, "ssm_group_solve")
+        return outs, [infos[i].as_dict() for i in range(n)], st
+
+    def device_bytes(self):
+        b = ctypes.c_int64()
+        st = load_library().ssm_group_device_bytes(self._h, ctypes.byref(b))
+        if st != SSM_OK:
+            raise SsmError(st, "ssm_group_device_bytes")
+        return b.value
+
+    def close(self):
+        if self._h:
+            load_library().ssm_group_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
