@@ -816,7 +816,9 @@ def cpu_baseline_and_errors(K, M, w, Md, F, make_plan, forms):
 # serving: Poisson-arriving solves of mixed shapes through the continuous-batching server
 # --------------------------------------------------------------------------------------
 SERVE_SHAPES = ["dr2d_tiny", "dr2d_slice", "rr3d_t1t2"]
-SERVE_FORMS = [("lowrank", "tf32x3"), ("dense", "bf16x3")]
+# (form, precision, group_small): the last runs the FP32 low-rank form with the small
+# requests solved in groups of up to 16
+SERVE_FORMS = [("lowrank", "tf32x3", 0), ("dense", "bf16x3", 0), ("lowrank", "fp32", 16)]
 SERVE_SEED = 46
 
 
@@ -850,13 +852,13 @@ def bench_serving(args):
            "io": "device buffers: M resident on the device, F written to a fresh device "
                  "buffer per request (ssm_server_submit_device)",
            "forms": {}}
-    for form, prec in SERVE_FORMS:
-        key = form_key(form, prec)
+    for form, prec, group in SERVE_FORMS:
+        key = form_key(form, prec) + ("_grouped" if group else "")
         kw = dict(form=form, precision=prec, max_iter=iters, check_every=0)
         free, _ = torch.cuda.mem_get_info()
         # plans get 60 % of the free memory; the rest holds the requests' F buffers
         with ssm.Server(max_active=4, use_graphs=True, cache_plans=True,
-                        hbm_budget=int(0.6 * free)) as srv:
+                        hbm_budget=int(0.6 * free), group_small=group) as srv:
             # solo service time per shape (plans built and cached here, as a server
             # running before the measurement would have them)
             solo = {}
@@ -920,7 +922,10 @@ def bench_serving(args):
             "hbm_budget_gb": st["budget"] / 1e9,
             "launch": "stream priority by footprint class (<= 64 MiB highest, one level per "
                       "factor 4 above); above the first class, persistent kernels in 8 "
-                      "launch waves; one of the 4 workers reserved for the first class",
+                      "launch waves; one of the 4 workers reserved for the first class" +
+                      (f"; first-class requests solved in groups of up to {group}"
+                       if group else ""),
+            "group_sizes": sorted({int(i["group_size"]) for i in infos}),
         }
         torch.cuda.empty_cache()
     return out
@@ -977,7 +982,63 @@ def bench_batching():
         out["forms"][form_key(form, prec)] = {
             "one_by_one_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
             "one_by_one_value": work / t_seq, "batched_value": work / t_bat}
+    out["heterogeneous_group"] = bench_group()
     return out
+
+
+GROUP_SHAPES = [((32, 32), 30, 225), ((24, 20), 16, 100), ((48, 16), 24, 64), ((64,), 12, 50),
+                ((12, 10, 6), 20, 80), ((40, 40), 30, 144)]
+
+
+def bench_group(nprob=64, iters=300):
+    """64 small problems of six shapes (differing N, P, Q; seed 51), 300 iterations each
+    (the low-rank FP32 form): solved one after another (ssm_solve, CUDA graphs) against
+    one group (ssm_group_*: one launch per iteration for all of them)."""
+    import torch
+
+    from paper_2401_12890_gb300 import ssm, synth
+    rng = np.random.default_rng(51)
+    kinds = rng.integers(0, len(GROUP_SHAPES), size=nprob)
+    plans, Ms, Fs, work = [], [], [], 0
+    for i, k in enumerate(kinds):
+        dims, P, Q = GROUP_SHAPES[k]
+        K, M, _ = synth.random_problem(P, Q, dims, seed=1000 + i, snr=60.0)
+        pl = ssm.Plan(K, dims, 0.02, 0.3, form="lowrank", precision="fp32", max_iter=iters,
+                      check_every=0)
+        pl.set_graphs(True)
+        plans.append(pl)
+        Ms.append(torch.from_numpy(np.ascontiguousarray(M, np.float32)).cuda())
+        Fs.append(torch.empty((Q, pl.N), dtype=torch.float32, device="cuda"))
+        work += pl.N * Q * iters
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for pl, M, F in zip(plans, Ms, Fs):
+        pl.solve_async(M, F)
+    torch.cuda.synchronize()
+    e0.record()
+    for pl, M, F in zip(plans, Ms, Fs):
+        pl.solve_async(M, F)
+    e1.record()
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    grp = ssm.Group(plans)
+    grp.solve(Ms, Fs)
+    torch.cuda.synchronize()
+    n0 = ssm.launch_count()
+    e0.record()
+    grp.solve(Ms, Fs)
+    e1.record()
+    torch.cuda.synchronize()
+    t_grp = e0.elapsed_time(e1) / 1e3
+    launches = ssm.launch_count() - n0
+    grp.close()
+    for pl in plans:
+        pl.close()
+    return {"problems": nprob, "iterations": iters,
+            "shapes": [{"dims": list(d), "P": P, "Q": Q} for d, P, Q in GROUP_SHAPES],
+            "mix": [int((kinds == j).sum()) for j in range(len(GROUP_SHAPES))],
+            "one_by_one_s": t_seq, "group_s": t_grp, "speedup": t_seq / t_grp,
+            "one_by_one_value": work / t_seq, "group_value": work / t_grp, "unit": METRIC,
+            "group_launches": launches}
 
 
 # --------------------------------------------------------------------------------------

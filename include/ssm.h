@@ -461,7 +461,9 @@ ssm_status ssm_destroy(ssm_plan_t plan);
  * it without planning again. Idle plans are evicted least recently used first when a
  * new request needs their memory. Each request's result is exactly what ssm_solve_host
  * (or ssm_solve) gives for it alone on a plan made with the same launch waves: the
- * kernels and launch shapes do not depend on what else runs.
+ * kernels and launch shapes do not depend on what else runs. With `group_small`, small
+ * low-rank requests are solved in groups (one launch per iteration for a whole group);
+ * their results are exactly those of a group of one, whatever else is in the group.
  * ------------------------------------------------------------------------------------
  */
 typedef struct ssm_server_s* ssm_server_t;
@@ -486,6 +488,13 @@ typedef struct {
                               request never queues behind large ones holding every
                               worker); < 0 selects 1 when max_active >= 2; at most
                               max_active - 1                                         */
+  int group_small;         /* > 1: a worker that admits a class-0 low-rank FP32 request
+                              with device buffers also admits up to group_small - 1
+                              more such requests waiting behind it, and solves them
+                              as one group (ssm_group_*: one launch per iteration for
+                              all); such a request then always runs in a group, alone
+                              or not, so its result does not depend on the others.
+                              0 or 1: off (the default)                             */
 } ssm_server_config;
 
 typedef struct {
@@ -501,6 +510,8 @@ typedef struct {
   int64_t order;           /* admission sequence number, from 0                     */
   int slot;                /* worker that ran the solve                             */
   int plan_reused;         /* 1 if a resident plan was reused                       */
+  int group_size;          /* requests solved together with it in one group (itself
+                              included); 0 when it ran on its own (ssm_solve)       */
 } ssm_request_info;
 
 typedef struct {

@@ -130,9 +130,10 @@ ssm_status create_impl(ssm_group_s* g, cudaStream_t s) {
     const int P = pl->P, Q = pl->Q, r = pl->r;
     const int64_t ld = pl->g.ld;
     g->ntiles[i] = (pl->g.N + kTableTile - 1) / kTableTile;
-    // the problem's own padded rank, not the group's: its launch shape (and so its
-    // summation order) does not depend on the other problems
-    g->nseg[i] = table_segments(g->ntiles[i], Q, table_padded_rank(r));
+    // segments from the problem's own Q alone (at least 32 compartments per warp: the
+    // group, not the segments, fills the device), so its launch shape and summation
+    // order do not depend on the other problems
+    g->nseg[i] = std::max(1, std::min(8, Q / 128));
     entries += g->ntiles[i] * g->nseg[i];
     SSM_TRY(galloc(g, &g->S[i], (size_t)R * ld, s));
     SSM_TRY(galloc(g, &g->V[i], (size_t)Q * R, s));

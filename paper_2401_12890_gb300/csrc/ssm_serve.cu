@@ -24,6 +24,13 @@
 // (stream priorities and launch waves help only a request that is already running).
 // The other workers take any request, first come first served.
 //
+// Groups (group_small > 1): a worker that admits a class-0 low-rank FP32 request with
+// device buffers also admits up to group_small - 1 such requests queued behind it (those
+// that fit the budget without evicting), and solves them together with ssm_group_*: one
+// launch per iteration for the whole group instead of one per request. Such a request
+// always runs in a group (of one when nothing else waits), and a problem's bits do not
+// depend on the rest of its group, so its result does not depend on the traffic.
+//
 // Memory accounting: every plan (running or idle) has a reservation, its peak
 // footprint while planning and its persistent footprint afterwards. `held` sums the
 // reservations of live plans, `dying` those of evicted plans not yet freed. A worker
@@ -110,6 +117,7 @@ struct Request {
   uint64_t khash = 0;
   int64_t footprint = 0;     // peak estimate (reserved at admission)
   int bypassed = 0;
+  int group_size = 0;        // > 0: solved in a group of this many requests
   bool done = false;
   Clock::time_point t_submit, t_admit, t_done;
   ssm_request_info info{};
@@ -212,27 +220,161 @@ struct ssm_server_s {
     return false;
   }
 
+  // a request the group path takes: class 0, low-rank FP32, device buffers (any
+  // buffers in the scheduler test mode, which moves no data)
+  bool groupable(const Request* q) const {
+    return cfg.group_small > 1 && q->level == 0 && (q->device_io || cfg.simulate_us > 0) &&
+           q->p.form == SSM_FORM_LOWRANK && q->p.precision != SSM_TF32X3;
+  }
+
+  // a resident plan for q that is idle and matches (caller holds mu)
+  Resident* find_match(const Request* q) {
+    if (!cfg.cache_plans) return nullptr;
+    for (auto& r : residents)
+      if (!r->busy && r->khash == q->khash && r->waves == q->waves && same_plan(r->p, q->p) &&
+          r->K.size() == (size_t)q->p.P * q->p.Q &&
+          std::memcmp(r->K.data(), q->K, sizeof(double) * r->K.size()) == 0)
+        return r.get();
+    return nullptr;
+  }
+
+  // after `first` was admitted: admit up to group_small - 1 more groupable requests
+  // waiting behind it that fit the budget without evicting (caller holds mu)
+  void admit_group(std::vector<std::pair<Request*, Resident*>>* members) {
+    for (size_t i = 0; i < pending.size() && (int)members->size() < cfg.group_small;) {
+      Request* q = pending[i];
+      if (!groupable(q)) {
+        ++i;
+        continue;
+      }
+      Resident* match = find_match(q);
+      const int64_t need = match ? 0 : q->footprint;
+      if (need > budget - held - dying) {
+        ++i;
+        continue;
+      }
+      if (match) {
+        match->busy = true;
+        q->info.plan_reused = 1;
+        ++st.plans_reused;
+      } else {
+        auto r = std::make_unique<Resident>();
+        r->p = q->p;
+        r->waves = q->waves;
+        r->khash = q->khash;
+        r->bytes = need;
+        r->busy = true;
+        held += need;
+        match = r.get();
+        residents.push_back(std::move(r));
+      }
+      peak = std::max(peak, held);
+      pending.erase(pending.begin() + (std::ptrdiff_t)i);
+      members->push_back({q, match});
+    }
+  }
+
+  // make q's plan if it has none (on `stream`); records plan_ms and trims the reservation
+  ssm_status ensure_plan(Request* q, Resident* res, cudaStream_t stream) {
+    if (res->plan) return SSM_OK;
+    const Clock::time_point t0 = Clock::now();
+    res->K.assign(q->K, q->K + (size_t)q->p.P * q->p.Q);
+    SSM_TRY(plan_create(&res->plan, &q->p, q->K, cfg.device, stream, q->waves));
+    q->info.plan_ms = ms_between(t0, Clock::now());
+    if (cfg.use_graphs) ssm_plan_set_graphs(res->plan, 1);
+    // planning's temporaries are gone: keep only the persistent reservation
+    ssm_params pr = q->p;
+    if (pr.form == SSM_FORM_LOWRANK) pr.rank = res->plan->r;
+    int64_t persistent = 0, peak_b = 0;
+    if (plan_footprint(pr, true, q->waves, &persistent, &peak_b) == SSM_OK &&
+        persistent < res->bytes) {
+      std::lock_guard<std::mutex> lk(mu);
+      held -= res->bytes - persistent;
+      res->bytes = persistent;
+    }
+    return SSM_OK;
+  }
+
+  // solve admitted groupable requests as one group; statuses per member in `out`
+  void run_group(std::vector<std::pair<Request*, Resident*>>& members, int slot,
+                 std::vector<ssm_status>* out) {
+    const bool sim = cfg.simulate_us > 0;
+    const size_t n = members.size();
+    out->assign(n, SSM_OK);
+    if (sim) {
+      int longest = 0;
+      for (auto& m : members) {
+        if (m.second->K.empty()) m.second->K.assign(m.first->K, m.first->K + (size_t)m.first->p.P * m.first->p.Q);
+        longest = std::max(longest, m.first->p.max_iter);
+        m.first->info.iterations = 0;
+        m.first->info.res_primal = m.first->info.res_change = -1;
+        m.first->group_size = (int)n;
+      }
+      std::this_thread::sleep_for(std::chrono::microseconds((int64_t)longest * cfg.simulate_us));
+      return;
+    }
+    cudaStream_t stream = streams[0][slot];
+    std::vector<size_t> idx;          // members that go into the group
+    std::vector<ssm_plan_t> plans;
+    for (size_t i = 0; i < n; ++i) {
+      Request* q = members[i].first;
+      Resident* res = members[i].second;
+      const ssm_status ps = ensure_plan(q, res, stream);
+      if (ps != SSM_OK) {
+        (*out)[i] = ps;
+        continue;
+      }
+      ssm_plan_s* pl = res->plan;
+      pl->p.max_iter = q->p.max_iter;
+      pl->p.check_every = q->p.check_every;
+      pl->p.tol_primal = q->p.tol_primal;
+      pl->p.tol_change = q->p.tol_change;
+      if (pl->r > 32 || pl->mask) {       // not a group problem: solved on its own
+        (*out)[i] = run(q, res, slot);
+        continue;
+      }
+      idx.push_back(i);
+      plans.push_back(pl);
+    }
+    if (idx.empty()) return;
+    ssm_group_t grp = nullptr;
+    ssm_status gs = ssm_group_create(&grp, (int)plans.size(), plans.data(), stream);
+    std::vector<const float*> Ms;
+    std::vector<float*> Fs;
+    std::vector<int64_t> lms, lfs;
+    std::vector<ssm_info> infos(idx.size());
+    for (size_t i : idx) {
+      Ms.push_back(members[i].first->M);
+      Fs.push_back(members[i].first->F);
+      lms.push_back(members[i].first->ldm);
+      lfs.push_back(members[i].first->ldf);
+    }
+    if (gs == SSM_OK)
+      gs = ssm_group_solve(grp, Ms.data(), lms.data(), Fs.data(), lfs.data(), infos.data(),
+                           stream);
+    ssm_group_destroy(grp);
+    for (size_t j = 0; j < idx.size(); ++j) {
+      Request* q = members[idx[j]].first;
+      q->group_size = (int)idx.size();
+      if (gs != SSM_OK && gs != SSM_ENOTCONVERGED && infos[j].iterations == 0 &&
+          infos[j].status == SSM_OK) {
+        (*out)[idx[j]] = gs;              // the group itself failed
+        continue;
+      }
+      (*out)[idx[j]] = (ssm_status)infos[j].status;
+      q->info.iterations = infos[j].iterations;
+      q->info.res_primal = infos[j].res_primal;
+      q->info.res_change = infos[j].res_change;
+    }
+  }
+
   // run one admitted request on `slot`'s stream; returns the solve's status
   ssm_status run(Request* q, Resident* res, int slot) {
     const bool sim = cfg.simulate_us > 0;
     cudaStream_t stream = sim ? nullptr : streams[q->level][slot];
-    if (!res->plan && !sim) {
-      const Clock::time_point t0 = Clock::now();
-      res->K.assign(q->K, q->K + (size_t)q->p.P * q->p.Q);
-      SSM_TRY(plan_create(&res->plan, &q->p, q->K, cfg.device, stream, q->waves));
-      q->info.plan_ms = ms_between(t0, Clock::now());
-      if (cfg.use_graphs) ssm_plan_set_graphs(res->plan, 1);
-      // planning's temporaries are gone: keep only the persistent reservation
-      ssm_params pr = q->p;
-      if (pr.form == SSM_FORM_LOWRANK) pr.rank = res->plan->r;
-      int64_t persistent = 0, peak_b = 0;
-      if (plan_footprint(pr, true, q->waves, &persistent, &peak_b) == SSM_OK &&
-          persistent < res->bytes) {
-        std::lock_guard<std::mutex> lk(mu);
-        held -= res->bytes - persistent;
-        res->bytes = persistent;
-      }
-    } else if (sim && res->K.empty()) {
+    if (!sim) {
+      SSM_TRY(ensure_plan(q, res, stream));
+    } else if (res->K.empty()) {
       res->K.assign(q->K, q->K + (size_t)q->p.P * q->p.Q);
     }
     if (sim) {
@@ -257,6 +399,40 @@ struct ssm_server_s {
     return s;
   }
 
+  // bookkeeping of a finished request (caller holds mu); returns a plan to free
+  std::unique_ptr<Resident> finish(Request* q, Resident* res, ssm_status s,
+                                   const std::string& err) {
+    const bool sim = cfg.simulate_us > 0;
+    std::unique_ptr<Resident> drop;
+    q->t_done = Clock::now();
+    q->info.status = s;
+    q->info.group_size = q->group_size;
+    q->info.queue_ms = ms_between(q->t_submit, q->t_admit);
+    q->info.solve_ms = ms_between(q->t_admit, q->t_done);
+    q->info.latency_ms = ms_between(q->t_submit, q->t_done);
+    q->error = err;
+    q->done = true;
+    res->busy = false;
+    res->last_used = ++tick;
+    const bool bad = s != SSM_OK && s != SSM_ENOTCONVERGED;
+    if (!q->info.plan_reused && (res->plan || sim) && !bad) ++st.plans_created;
+    if (bad) ++st.failed;
+    else ++st.completed;
+    // a plan that failed to build, or any plan when caching is off, is freed now
+    if (!cfg.cache_plans || (!res->plan && !sim) || bad) {
+      for (auto it = residents.begin(); it != residents.end(); ++it)
+        if (it->get() == res) {
+          held -= res->bytes;
+          dying += res->bytes;
+          drop = std::move(*it);
+          residents.erase(it);
+          break;
+        }
+    }
+    --active;
+    return drop;
+  }
+
   void worker(int slot) {
     const bool sim = cfg.simulate_us > 0;
     if (!sim) cudaSetDevice(cfg.device);
@@ -264,16 +440,23 @@ struct ssm_server_s {
       Request* q = nullptr;
       Resident* res = nullptr;
       std::vector<std::unique_ptr<Resident>> evict;
+      std::vector<std::pair<Request*, Resident*>> members;
+      bool group = false;
       {
         std::unique_lock<std::mutex> lk(mu);
         cv_work.wait(lk, [&] {
           return stop || (!pending.empty() && try_admit(slot, &q, &res, &evict));
         });
         if (!q) return;   // stop
-        ++active;
-        q->t_admit = Clock::now();
-        q->info.order = next_order++;
-        q->info.slot = slot;
+        members.push_back({q, res});
+        group = groupable(q);
+        if (group) admit_group(&members);
+        for (auto& m : members) {
+          ++active;
+          m.first->t_admit = Clock::now();
+          m.first->info.order = next_order++;
+          m.first->info.slot = slot;
+        }
       }
       if (!evict.empty()) {
         int64_t freed = 0;
@@ -284,41 +467,27 @@ struct ssm_server_s {
         std::lock_guard<std::mutex> lk(mu);
         dying -= freed;
       }
-      const ssm_status s = run(q, res, slot);
-      const std::string err = s == SSM_OK || s == SSM_ENOTCONVERGED ? "" : ssm_last_error();
-      std::unique_ptr<Resident> drop;
+      std::vector<ssm_status> sts;
+      std::vector<std::string> errs;
+      if (group) {
+        run_group(members, slot, &sts);
+      } else {
+        sts.push_back(run(q, res, slot));
+      }
+      for (ssm_status s : sts)
+        errs.push_back(s == SSM_OK || s == SSM_ENOTCONVERGED ? "" : ssm_last_error());
+      std::vector<std::unique_ptr<Resident>> drops;
       {
         std::lock_guard<std::mutex> lk(mu);
-        q->t_done = Clock::now();
-        q->info.status = s;
-        q->info.queue_ms = ms_between(q->t_submit, q->t_admit);
-        q->info.solve_ms = ms_between(q->t_admit, q->t_done);
-        q->info.latency_ms = ms_between(q->t_submit, q->t_done);
-        q->error = err;
-        q->done = true;
-        res->busy = false;
-        res->last_used = ++tick;
-        const bool bad = s != SSM_OK && s != SSM_ENOTCONVERGED;
-        if (!q->info.plan_reused && (res->plan || sim) && !bad) ++st.plans_created;
-        if (bad) ++st.failed;
-        else ++st.completed;
-        // a plan that failed to build, or any plan when caching is off, is freed now
-        if (!cfg.cache_plans || (!res->plan && !sim) || bad) {
-          for (auto it = residents.begin(); it != residents.end(); ++it)
-            if (it->get() == res) {
-              held -= res->bytes;
-              dying += res->bytes;
-              drop = std::move(*it);
-              residents.erase(it);
-              break;
-            }
+        for (size_t i = 0; i < members.size(); ++i) {
+          auto d = finish(members[i].first, members[i].second, sts[i], errs[i]);
+          if (d) drops.push_back(std::move(d));
         }
-        --active;
       }
-      if (drop) {
-        if (drop->plan) ssm_destroy(drop->plan);
+      for (auto& d : drops) {
+        if (d->plan) ssm_destroy(d->plan);
         std::lock_guard<std::mutex> lk(mu);
-        dying -= drop->bytes;
+        dying -= d->bytes;
       }
       cv_done.notify_all();
       cv_work.notify_all();
@@ -429,6 +598,7 @@ ssm_status ssm_server_default_config(ssm_server_config* c) {
   c->small_bytes = (int64_t)1 << 26;
   c->large_waves = 8;
   c->reserved_small = -1;
+  c->group_small = 0;
   return SSM_OK;
 }
 

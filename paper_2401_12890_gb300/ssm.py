@@ -60,7 +60,7 @@ class SsmServerConfig(ctypes.Structure):
         ("use_graphs", ctypes.c_int), ("cache_plans", ctypes.c_int),
         ("max_bypass", ctypes.c_int), ("simulate_us", ctypes.c_int64),
         ("small_bytes", ctypes.c_int64), ("large_waves", ctypes.c_int),
-        ("reserved_small", ctypes.c_int),
+        ("reserved_small", ctypes.c_int), ("group_small", ctypes.c_int),
     ]
 
 
@@ -71,7 +71,7 @@ class SsmRequestInfo(ctypes.Structure):
         ("queue_ms", ctypes.c_double), ("plan_ms", ctypes.c_double),
         ("solve_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
         ("footprint", ctypes.c_int64), ("order", ctypes.c_int64), ("slot", ctypes.c_int),
-        ("plan_reused", ctypes.c_int),
+        ("plan_reused", ctypes.c_int), ("group_size", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -561,7 +561,7 @@ class Server:
 
     def __init__(self, *, device=0, max_active=4, hbm_budget=0, use_graphs=True,
                  cache_plans=True, max_bypass=-1, simulate_us=0, small_bytes=None,
-                 large_waves=None, reserved_small=None):
+                 large_waves=None, reserved_small=None, group_small=None):
         lib = load_library()
         c = SsmServerConfig()
         lib.ssm_server_default_config(ctypes.byref(c))
@@ -574,6 +574,8 @@ class Server:
             c.large_waves = int(large_waves)
         if reserved_small is not None:
             c.reserved_small = int(reserved_small)
+        if group_small is not None:
+            c.group_small = int(group_small)
         self._h = ctypes.c_void_p()
         st = lib.ssm_server_create(ctypes.byref(self._h), ctypes.byref(c))
         if st != SSM_OK:

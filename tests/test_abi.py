@@ -34,13 +34,14 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layout_matches_header(lib, tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ssm.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                    ' sizeof(ssm_params), sizeof(ssm_info), offsetof(ssm_params, tol_change),'
                    ' offsetof(ssm_info, plan_ms), sizeof(ssm_server_config),'
                    ' offsetof(ssm_server_config, reserved_small), sizeof(ssm_request_info),'
                    ' offsetof(ssm_request_info, plan_reused), sizeof(ssm_server_stats),'
                    ' offsetof(ssm_server_stats, pending), sizeof(ssm_launch_info),'
-                   ' offsetof(ssm_launch_info, tc_fused), offsetof(ssm_info, power_converged));'
+                   ' offsetof(ssm_launch_info, tc_fused), offsetof(ssm_info, power_converged),'
+                   ' offsetof(ssm_server_config, group_small), offsetof(ssm_request_info, group_size));'
                    ' return 0;}\n')
     exe = tmp_path / "sz"
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
@@ -53,7 +54,8 @@ def test_struct_layout_matches_header(lib, tmp_path):
                     ctypes.sizeof(ssm.SsmRequestInfo), ssm.SsmRequestInfo.plan_reused.offset,
                     ctypes.sizeof(ssm.SsmServerStats), ssm.SsmServerStats.pending.offset,
                     ctypes.sizeof(ssm.SsmLaunchInfo), ssm.SsmLaunchInfo.tc_fused.offset,
-                    ssm.SsmInfo.power_converged.offset]
+                    ssm.SsmInfo.power_converged.offset, ssm.SsmServerConfig.group_small.offset,
+                    ssm.SsmRequestInfo.group_size.offset]
 
 
 def test_defaults_and_status_strings(lib):

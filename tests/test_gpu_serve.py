@@ -287,3 +287,49 @@ def test_tune_beta_matches_the_oracle(name, dims):
     assert best == pytest.approx(ref_best, rel=1e-12) or \
         table[ref_b[k]] <= table[ref_best] * (1 + 1e-5)
     print(f"{name}: beta {best:.4g} (oracle {ref_best:.4g}), J {J.min():.6g}")
+
+
+def test_grouped_small_requests():
+    """group_small: small low-rank requests with device buffers are solved in groups.
+    Each result is bitwise that of a group of one (ssm_group_*) for the same problem, and
+    within the FP32 bar of the oracle; large requests are not grouped."""
+    rng = np.random.default_rng(77)
+    shapes = [((32, 32), 30, 225), ((20, 24), 12, 40), ((50,), 9, 30), ((9, 7, 4), 16, 20)]
+    reqs = []
+    for i in range(12):
+        dims, P, Q = shapes[i % len(shapes)]
+        if dims == (32, 32):
+            K, M, _ = synth.make_problem("dr2d_tiny")
+        else:
+            K, M, _ = synth.random_problem(P, Q, dims, seed=100 + i, snr=60.0)
+        kw = dict(form="lowrank", max_iter=int(rng.integers(40, 120)), check_every=10,
+                  tol_primal=1e-9 if i % 3 else 2e-3, tol_change=1e-9 if i % 3 else 2e-3)
+        reqs.append(dict(K=K, M=np.ascontiguousarray(M, np.float32), dims=dims, lam=0.02,
+                         beta=0.3, kw=kw))
+    big = synth.WORKLOADS["dr2d_slice"]
+    Kb, Mb, _ = synth.make_problem("dr2d_slice")
+    out = []
+    with ssm.Server(max_active=2, small_bytes=SMALL_BYTES, large_waves=LARGE_WAVES,
+                    group_small=8) as srv:
+        tb = srv.submit(Kb, torch.from_numpy(Mb).cuda(), big.dims, big.lam, big.beta,
+                        form="lowrank", max_iter=300, check_every=0)
+        tickets = [srv.submit(r["K"], torch.from_numpy(r["M"]).cuda(), r["dims"], r["lam"],
+                              r["beta"], **r["kw"]) for r in reqs]
+        for t in tickets:
+            out.append(srv.wait(t))
+        _, binfo = srv.wait(tb)
+    assert binfo["group_size"] == 0 and binfo["status"] == ssm.SSM_OK
+    assert max(info["group_size"] for _, info in out) > 1    # some ran together
+    for r, (F, info) in zip(reqs, out):
+        assert info["status"] in (ssm.SSM_OK, ssm.SSM_ENOTCONVERGED)
+        assert info["group_size"] >= 1
+        plan = ssm.Plan(r["K"], r["dims"], r["lam"], r["beta"], **r["kw"])
+        grp = ssm.Group([plan])
+        Fs, infos, _ = grp.solve([torch.from_numpy(r["M"]).cuda()])
+        grp.close()
+        plan.close()
+        assert info["iterations"] == infos[0]["iterations"]
+        assert torch.equal(F, Fs[0])
+        ref = L.ladmm(r["K"], r["M"].astype(np.float64), r["dims"], r["lam"], r["beta"],
+                      iters=info["iterations"], check_every=0)
+        assert rel(F.cpu().numpy(), ref["z"]) <= RTOL

@@ -209,3 +209,32 @@ def test_reserved_workers_never_take_every_worker():
         info = srv.wait(srv.submit(*problem(*BIG[:2], BIG[2], 1), BIG[2], 0.01, 1.0,
                                    max_iter=2))[1]
     assert info["status"] == ssm.SSM_OK and info["slot"] == 1
+
+
+def test_small_requests_are_admitted_as_groups():
+    """group_small = 4: requests waiting behind a busy worker are admitted four at a time
+    and solved as one group; large ones are never grouped."""
+    big_b, small_b = footprints()
+    with ssm.Server(max_active=1, hbm_budget=1 << 40, simulate_us=TICK_US, cache_plans=False,
+                    small_bytes=2 * small_b, group_small=4) as srv:
+        first = srv.submit(*problem(*SMALL[:2], SMALL[2], 0), SMALL[2], 0.01, 1.0, max_iter=30)
+        time.sleep(0.01)
+        rest = [srv.submit(*problem(*SMALL[:2], SMALL[2], i), SMALL[2], 0.01, 1.0, max_iter=3)
+                for i in range(1, 6)]
+        big = srv.submit(*problem(*BIG[:2], BIG[2], 9), BIG[2], 0.01, 1.0, max_iter=2)
+        infos = [srv.wait(t)[1] for t in [first] + rest + [big]]
+    sizes = [i["group_size"] for i in infos]
+    assert sizes[0] == 1                 # alone when admitted: a group of one
+    assert sizes[1:5] == [4, 4, 4, 4]    # the next four together
+    assert sizes[5] == 1 and sizes[6] == 0
+    orders = [i["order"] for i in infos]
+    assert orders[1:5] == [1, 2, 3, 4]
+    # the group ran as one solve: its members finished together
+    assert max(i["latency_ms"] for i in infos[1:5]) - min(i["latency_ms"] for i in infos[1:5]) \
+        < 10 * TICK_US * 1e-3
+
+
+def test_groups_are_off_by_default():
+    with ssm.Server(max_active=1, hbm_budget=1 << 40, simulate_us=TICK_US) as srv:
+        infos = run_all(srv, [(*problem(*SMALL[:2], SMALL[2], i), SMALL[2], 2) for i in range(3)])
+    assert [i["group_size"] for i in infos] == [0, 0, 0]
