@@ -31,7 +31,8 @@ struct ssm_group_s {
   int64_t* ranges = nullptr;            // per active problem: first row, rows (device)
   double* red = nullptr;                // residual partial rows (4 doubles per entry)
   double* sums = nullptr;               // 3 doubles per problem (device)
-  double* sums_host = nullptr;          // pinned
+  std::vector<double> sums_host;        // their host copy
+  cudaStream_t stream = nullptr;        // the stream of the last create/solve call
   int64_t bytes = 0;
 };
 
@@ -75,21 +76,22 @@ ssm_status galloc(ssm_group_s* g, T** p, size_t count, cudaStream_t s) {
   return SSM_OK;
 }
 
+// frees stream-ordered on the stream the group last ran on, so that releasing a group
+// waits for nothing else on the device (a device-wide synchronisation here would hold a
+// serving worker behind every other worker's solve)
 void group_release(ssm_group_s* g) {
   if (!g) return;
   cudaSetDevice(g->device);
-  cudaDeviceSynchronize();
+  cudaStream_t s = g->stream;
   for (auto* v : {&g->S, &g->V, &g->cA, &g->cW, &g->U0, &g->U1})
     for (float* p : *v)
-      if (p) cudaFree(p);
+      if (p) cudaFreeAsync(p, s);
   for (double* p : g->B)
-    if (p) cudaFree(p);
-  if (g->probs) cudaFree(g->probs);
-  if (g->table) cudaFree(g->table);
-  if (g->ranges) cudaFree(g->ranges);
-  if (g->red) cudaFree(g->red);
-  if (g->sums) cudaFree(g->sums);
-  if (g->sums_host) cudaFreeHost(g->sums_host);
+    if (p) cudaFreeAsync(p, s);
+  for (void* p : {(void*)g->probs, (void*)g->table, (void*)g->ranges, (void*)g->red,
+                  (void*)g->sums})
+    if (p) cudaFreeAsync(p, s);
+  cudaStreamSynchronize(s);
   delete g;
 }
 
@@ -183,7 +185,7 @@ ssm_status create_impl(ssm_group_s* g, cudaStream_t s) {
   SSM_TRY(galloc(g, &g->ranges, (size_t)2 * np, s));
   SSM_TRY(galloc(g, &g->red, (size_t)entries * 4, s));
   SSM_TRY(galloc(g, &g->sums, (size_t)3 * np, s));
-  SSM_CUDA(cudaMallocHost(&g->sums_host, sizeof(double) * 3 * np));
+  g->sums_host.assign((size_t)3 * np, 0.0);
   SSM_CUDA(cudaMemcpyAsync(g->probs, tp.data(), sizeof(TableProblem) * np,
                            cudaMemcpyHostToDevice, s));
   SSM_CUDA(cudaStreamSynchronize(s));   // `tp` is a host temporary
@@ -260,7 +262,7 @@ ssm_status solve_impl(ssm_group_s* g, const float* const* M, const int64_t* ldm,
     if (!check) continue;
     group_finish_kernel<<<(unsigned)act.size(), FT, 0, s>>>(g->red, g->ranges, g->sums);
     SSM_LAUNCHED();
-    SSM_CUDA(cudaMemcpyAsync(g->sums_host, g->sums, sizeof(double) * 3 * act.size(),
+    SSM_CUDA(cudaMemcpyAsync(g->sums_host.data(), g->sums, sizeof(double) * 3 * act.size(),
                              cudaMemcpyDeviceToHost, s));
     SSM_CUDA(cudaStreamSynchronize(s));
     bool changed = false;
@@ -269,7 +271,7 @@ ssm_status solve_impl(ssm_group_s* g, const float* const* M, const int64_t* ldm,
       const ssm_params& p = g->plans[i]->p;
       if (!is_check(p, k - 1)) continue;
       ProbRun& pr = run[i];
-      const double* h = g->sums_host + 3 * j;
+      const double* h = g->sums_host.data() + 3 * j;
       bool done = k == p.max_iter;
       if (!std::isfinite(h[0]) || !std::isfinite(h[1]) || !std::isfinite(h[2])) {
         pr.status = SSM_ENAN;
@@ -356,6 +358,7 @@ ssm_status ssm_group_create(ssm_group_t* out, int nplans, const ssm_plan_t* plan
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   auto* g = new ssm_group_s();
   g->device = device;
+  g->stream = s;
   g->plans.assign(plans, plans + nplans);
   const ssm_status st = create_impl(g, s);
   if (st != SSM_OK) {
@@ -385,7 +388,8 @@ ssm_status ssm_group_solve(ssm_group_t group, const float* const* M_devs, const 
     }
   }
   SSM_CUDA(cudaSetDevice(group->device));
-  return solve_impl(group, M_devs, ldms, F_devs, ldfs, infos, static_cast<cudaStream_t>(stream));
+  group->stream = static_cast<cudaStream_t>(stream);
+  return solve_impl(group, M_devs, ldms, F_devs, ldfs, infos, group->stream);
 }
 
 ssm_status ssm_group_device_bytes(ssm_group_t group, int64_t* bytes) {
