@@ -467,7 +467,7 @@ ssm_status multi_plan_impl(ssm_plan_s* pl, int ndict, const double* K_host,
   pl->n = std::min(P, Q);
   pl->ndict = ndict;
   pl->ranks.assign(ndict, 0);
-  // staging at stride RM: [c][q][i], [c][i], [c][p][i]
+  // staging at stride RM: V [q][c][i], weights [c][i], sigma_i u_i [c][p][i]
   float *Vs = nullptr, *As = nullptr, *Ws = nullptr;
   double* Bs = nullptr;
   auto free_staging = [&]() {
@@ -480,6 +480,7 @@ ssm_status multi_plan_impl(ssm_plan_s* pl, int ndict, const double* K_host,
   SSM_TRY(dalloc(&As, (size_t)ndict * RM, s));
   SSM_TRY(dalloc(&Ws, (size_t)ndict * RM, s));
   SSM_TRY(dalloc(&Bs, (size_t)ndict * P * RM, s));
+  SSM_CUDA(cudaMemsetAsync(Vs, 0, sizeof(float) * ndict * Q * RM, s));
   ssm_params sp = p;
   sp.ndim = 1;
   sp.dims[0] = sp.dims[1] = sp.dims[2] = 1;
@@ -500,11 +501,10 @@ ssm_status multi_plan_impl(ssm_plan_s* pl, int ndict, const double* K_host,
       pl->kk_power = std::max(pl->kk_power, sub->kk_power);
       pl->power_iters = std::max(pl->power_iters, sub->power_iters);
       pl->power_conv = c == 0 ? sub->power_conv : std::min(pl->power_conv, sub->power_conv);
-      cudaError_t e = cudaMemsetAsync(Vs + (size_t)c * Q * RM, 0, sizeof(float) * Q * RM, s);
-      if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(Vs + (size_t)c * Q * RM, sizeof(float) * RM, sub->V32,
-                              sizeof(float) * sub->R, sizeof(float) * r, Q,
-                              cudaMemcpyDeviceToDevice, s);
+      // V at [q][c][i]: row q of dictionary c at (q ndict + c) RM
+      cudaError_t e = cudaMemcpy2DAsync(Vs + (size_t)c * RM, sizeof(float) * RM * ndict,
+                                        sub->V32, sizeof(float) * sub->R, sizeof(float) * r, Q,
+                                        cudaMemcpyDeviceToDevice, s);
       if (e == cudaSuccess) e = cudaMemsetAsync(As + (size_t)c * RM, 0, sizeof(float) * RM, s);
       if (e == cudaSuccess) e = cudaMemsetAsync(Ws + (size_t)c * RM, 0, sizeof(float) * RM, s);
       if (e == cudaSuccess)
@@ -588,6 +588,7 @@ ssm_status multi_plan_impl(ssm_plan_s* pl, int ndict, const double* K_host,
   tp.g = pl->g;
   tp.Q = Q;
   tp.nseg = pl->mseg;
+  tp.ndict = ndict;
   tp.beta = (float)p.beta;
   tp.inv_beta = (float)(1.0 / p.beta);
   tp.xi = (float)pl->xi;

@@ -169,6 +169,7 @@ ssm_status create_impl(ssm_group_s* g, cudaStream_t s) {
     t.g = pl->g;
     t.Q = Q;
     t.nseg = g->nseg[i];
+    t.ndict = 1;
     t.beta = (float)pl->p.beta;
     t.inv_beta = (float)(1.0 / pl->p.beta);
     t.xi = (float)pl->xi;

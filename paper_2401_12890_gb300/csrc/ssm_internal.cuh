@@ -96,13 +96,15 @@ struct TableProblem {
   float* D[2];                      // d ping-pong (Q x ld; read/written around tests)
   float* U[2];                      // partial u per (tile, segment) [tile][seg][R][32]
   const float* S;                   // R x ld: S_i = sigma_i u_i^T m per voxel
-  const float* V;                   // ndict x Q x R  [c][q][i]
+  const float* V;                   // Q x ndict x R  [q][c][i]: a compartment's rows of
+                                    // every dictionary side by side
   const float* coefA;               // ndict x R: 1/(beta + sigma^2)
   const float* coefW;               // ndict x R: sigma^2/(beta^2 + beta sigma^2)
   const int32_t* labels;            // dictionary of each voxel (nullptr: dictionary 0)
   Grid g;
   int Q;
   int nseg;                         // compartment segments per tile
+  int ndict;                        // dictionaries (labels in [0, ndict))
   float beta, inv_beta, xi, lam_s, inv_xb;
 };
 
@@ -151,6 +153,7 @@ struct ssm_plan_s {
   float* K32 = nullptr;        // P x Q (objective with the full K)
   float* Kr32 = nullptr;       // P x Q (objective with K_r)
   float* V32 = nullptr;        // Q x R  [q][i]  low-rank right singular vectors
+                               // (multi plans: Q x ndict x R, [q][c][i])
   // TF32x3 low-rank form: V (Q x R) and V^T (R x lrtc_qs), split into TF32 hi/lo parts
   float* V1h = nullptr;
   float* V1l = nullptr;
@@ -212,7 +215,7 @@ struct ssm_plan_s {
   bool has_state = false;
   int cur_state = 0;           // ping-pong half holding z^k (and w^k, partial u)
   // spatially varying dictionaries (ssm_plan_multi): ndict > 0. V32, coefA and coefW
-  // then hold every dictionary's factors ([c][q][i], [c][i]), padded to the common R
+  // then hold every dictionary's factors ([q][c][i], [c][i]), padded to the common R
   int ndict = 0;
   int32_t* labels = nullptr;         // N dictionary labels
   double* B_multi = nullptr;         // ndict x P x R: sigma_{c,i} u_{c,i} (S = B^T m per voxel)

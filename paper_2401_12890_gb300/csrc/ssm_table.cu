@@ -150,7 +150,10 @@ __global__ void __launch_bounds__(VT * WPB, min_blocks<R>())
   // row pointers advance by ld (state) and R (basis) per compartment
   const int64_t nxl = nx;
   const float* zrow = Zin + (int64_t)qa * ld + n;
-  const float4* vrow = reinterpret_cast<const float4*>(P.V + ((int64_t)c * Q + qa) * R);
+  // basis rows: [q][c][i], a compartment's rows of all dictionaries side by side (the
+  // labels of a warp's voxels, quantised from a smooth field, are mostly neighbours)
+  const int64_t vstep = (int64_t)P.ndict * (R / 4);   // float4s from row q to row q + 1
+  const float4* vrow = reinterpret_cast<const float4*>(P.V + ((int64_t)qa * P.ndict + c) * R);
   float* zout = Zo + (int64_t)qa * ld + n;
   float* dout = Do ? Do + (int64_t)qa * ld + n : nullptr;
   const float* din = Din + (int64_t)qa * ld + n;
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(VT * WPB, min_blocks<R>())
   auto row = [&](int u, float z, float nb) {
     float4 vr[R / 4];
 #pragma unroll
-    for (int i = 0; i < R / 4; ++i) vr[i] = __ldg(vrow + u * (R / 4) + i);
+    for (int i = 0; i < R / 4; ++i) vr[i] = __ldg(vrow + u * vstep + i);
     float2 p0 = make_float2(0.f, 0.f), p1 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < R / 4; ++i) {
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(VT * WPB, min_blocks<R>())
     zout += (int64_t)k * ld;
     if (dout) dout += (int64_t)k * ld;
     din += (int64_t)k * ld;
-    vrow += k * (R / 4);
+    vrow += k * vstep;
   };
   if (in) {
     // UR rows' state loads issued together (memory-level parallelism of a latency-bound
