@@ -22,18 +22,20 @@
 // D^T D z = s (deg(n) z_n - sum_{m adjacent} z_m): the free-boundary grid Laplacian,
 // s = 2 for the literal Eq. 8.
 //
-// Mapping (HBM-streaming, TMA-fed, persistent). The work is the flattened list of
-// (voxel tile of 128, compartment) rows; each CTA of a grid sized to the resident
-// capacity takes an equal contiguous share, split into segments at tile boundaries.
-// One producer warp streams a segment's rows in stages of QC compartments with 2D TMA
+// Mapping (HBM-streaming, TMA-fed, persistent). The work units are (segment, voxel tile
+// of 128) pairs, a segment being one of nseg equal compartment ranges; the units are
+// dealt round-robin in segment-major order to a grid sized to the resident capacity, so
+// the CTAs of one round stream the same compartments of consecutive tiles and each
+// one's neighbour rows were just read by another (L2 hits); nseg is chosen by layout().
+// One producer warp streams a unit's rows in stages of QC compartments with 2D TMA
 // box loads -- z with its x halo, the -+nx (-+nx*ny) neighbour rows, d and the
 // matching rows of V -- into a ring of shared-memory stages guarded by mbarriers.
 // Four consumer warps own one voxel per lane: for every staged compartment they
 // compute f (packed f32x2 FMAs over the rank index), the z-step and the dual step,
 // store z' and d' (coalesced), and fold beta z' - d' into the voxel's u' accumulators
-// kept in registers. At the end of a segment the partial u' goes to a per-(tile,
-// segment) slot; the next iteration sums a tile's slots in segment order (fixed,
-// hence deterministic) when it forms a. HBM traffic per state element and iteration:
+// kept in registers. At the end of a unit the partial u' goes to its (tile, segment)
+// slot; the next iteration sums a tile's slots in segment order (fixed, hence
+// deterministic) when it forms a. HBM traffic per state element and iteration:
 // read z, write z' (8 B); d is read/written only around residual tests; the halo rows
 // are L2 hits. Every mbarrier wait is
 // bounded and reports SSM_ETIMEOUT through the plan's device error word.
@@ -67,8 +69,8 @@ struct LowrankArgs {
   const float* __restrict__ S;      // R x ld
   const float* __restrict__ Pin;    // partial u of the previous iteration [tile][seg][R][TV]
   float* __restrict__ Pout;         // partial u of this iteration
-  int64_t ntiles, T;                // tiles, total rows (ntiles * Q)
-  int maxseg;                       // segment slots per tile
+  int64_t ntiles;                   // voxel tiles
+  int nseg;                         // compartment segments per tile (units = ntiles nseg)
   const float* __restrict__ coefA;  // R
   const float* __restrict__ coefW;  // R
   double* __restrict__ partial;     // 4 doubles per block (check iterations)
@@ -100,14 +102,6 @@ __host__ __device__ __forceinline__ int64_t floor4(int64_t v) {
   return v >= 0 ? (v & ~(int64_t)3) : -(((-v) + 3) & ~(int64_t)3);
 }
 
-// contiguous share [lo, hi) of the flattened rows for CTA j of G
-__host__ __device__ __forceinline__ int64_t share_lo(int64_t T, int64_t j, int64_t G) {
-  return (T * j) / G;
-}
-// the first CTA whose share contains flattened row r
-__host__ __device__ __forceinline__ int64_t owner_of(int64_t r, int64_t T, int64_t G) {
-  return ((r + 1) * G + T - 1) / T - 1;
-}
 
 template <int R, bool CHECK>
 __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant__ LowrankMaps maps,
@@ -134,8 +128,16 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
   const int64_t off[4] = {ny > 1 ? -(int64_t)nx : -plane, ny > 1 ? (int64_t)nx : plane, -plane,
                           plane};
   const int64_t G = gridDim.x;
-  const int64_t lo = share_lo(a.T, blockIdx.x, G);
-  const int64_t hi = share_lo(a.T, blockIdx.x + 1, G);
+  const int64_t nunits = a.ntiles * a.nseg;
+  // unit u = (segment u / ntiles, tile u % ntiles), dealt round-robin: the CTAs of one
+  // round hold the same compartments of consecutive tiles, so the neighbour rows each
+  // stages were just streamed by another (L2 hits)
+  auto unit_rows = [&](int64_t u, int64_t& tile, int& sg, int& q0, int& q1) {
+    sg = (int)(u / a.ntiles);
+    tile = u - (int64_t)sg * a.ntiles;
+    q0 = (int)(((int64_t)Q * sg) / a.nseg);
+    q1 = (int)(((int64_t)Q * (sg + 1)) / a.nseg);
+  };
   // d^k is staged only on residual-test iterations (it enters f, not z' or u')
   const unsigned stage_bytes = (unsigned)(QC * ZW * 4 + NR * QC * NW * 4 +
                                           (CHECK ? QC * TV * 4 : 0) + QC * R * 4);
@@ -158,12 +160,12 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
     if (lane == 0) {
       tma_prefetch_map(&maps.zc);
       tma_prefetch_map(&maps.d);
-      int c = 0;   // running stage counter over all segments
-      for (int64_t r = lo; r < hi && !failed;) {
-        const int64_t tile = r / Q;
+      int c = 0;   // running stage counter over all units
+      for (int64_t u = blockIdx.x; u < nunits && !failed; u += G) {
+        int64_t tile;
+        int sg, q0, qend;
+        unit_rows(u, tile, sg, q0, qend);
         const int64_t n0 = tile * TV;
-        const int q0 = (int)(r - tile * Q);
-        const int qend = (int)(min(hi, (tile + 1) * Q) - tile * Q);
         for (int q = q0; q < qend; q += QC, ++c) {
           const int b = c % NB;
           const int k = c / NB;
@@ -180,18 +182,17 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
           if (CHECK) tma_load_2d(st + L.dd, &maps.d, (int)n0, q, &full[b]);
           tma_load_2d(st + L.vv, &maps.v, 0, q, &full[b]);
         }
-        r = tile * Q + qend;
       }
     }
   } else {
     // ------------------------------- consumer warps: one voxel per lane
     const int v = warp * 32 + lane;
     int c = 0;
-    for (int64_t r = lo; r < hi;) {
-      const int64_t tile = r / Q;
+    for (int64_t u = blockIdx.x; u < nunits; u += G) {
+      int64_t tile;
+      int sidx, q0, qend;
+      unit_rows(u, tile, sidx, q0, qend);
       const int64_t n0 = tile * TV;
-      const int q0 = (int)(r - tile * Q);
-      const int qend = (int)(min(hi, (tile + 1) * Q) - tile * Q);
       const int64_t n = n0 + v;
       const bool valid = n < N;
       int x = 0, y = 0, zc = 0;
@@ -225,16 +226,14 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
       }
       // a_i = S_i/(beta + sigma_i^2) - W_i u_i, u_i summed over the tile's segment
       // slots of the previous iteration in segment order
-      const int64_t j0 = owner_of(tile * Q, a.T, G);
-      const int nseg = (int)(owner_of(tile * Q + Q - 1, a.T, G) - j0 + 1);
-      const int sidx = (int)(blockIdx.x - j0);
+      const int nseg = a.nseg;
       float2 av[R / 2];
 #pragma unroll
       for (int i = 0; i < R / 2; ++i) {
         float a0 = 0.f, a1 = 0.f;
         if (in) {
           float u0 = 0.f, u1 = 0.f;
-          const float* pt = a.Pin + (tile * a.maxseg) * (int64_t)(R * TV);
+          const float* pt = a.Pin + (tile * nseg) * (int64_t)(R * TV);
           for (int sg = 0; sg < nseg; ++sg) {
             u0 += pt[(sg * R + 2 * i) * TV + v];
             u1 += pt[(sg * R + 2 * i + 1) * TV + v];
@@ -304,13 +303,12 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
         if (lane == 0) mbar_arrive(&empty[b]);
       }
       // this segment's partial u' (zero for voxels past the grid)
-      float* po = a.Pout + ((tile * a.maxseg + sidx) * (int64_t)R) * TV;
+      float* po = a.Pout + ((tile * nseg + sidx) * (int64_t)R) * TV;
 #pragma unroll
       for (int i = 0; i < R / 2; ++i) {
         po[(2 * i) * TV + v] = in ? uacc[i].x : 0.f;
         po[(2 * i + 1) * TV + v] = in ? uacc[i].y : 0.f;
       }
-      r = tile * Q + qend;
     }
   }
   if (failed) atomicExch(a.err, (int)SSM_ETIMEOUT);
@@ -405,28 +403,57 @@ int bpsm_for(int R, int nr) {
 
 }  // namespace
 
-// persistent grid: every resident slot, but at least two stages of rows per CTA
-int64_t lowrank_grid(const ssm_plan_s* pl) {
+namespace {
+
+// a unit's start (the a-vector from the segment slots, the partial u' at its end) costs
+// about as much as this many compartment rows
+constexpr int kUnitRows = 16;
+
+// Launch layout: G CTAs (every resident slot, times the launch waves) and nseg segments
+// per tile, the units (segment, tile) dealt round-robin. nseg minimises rounds x (rows
+// per unit + a unit's start), rounds = ceil(ntiles nseg / G): on the 128x128 slice
+// (128 tiles, 456 CTAs) 7 segments make 896 units, two rounds of 357 rows, against the
+// 702 rows per CTA of an even split that cannot keep neighbouring tiles in step.
+void layout(const ssm_plan_s* pl, int64_t* grid, int* nseg) {
   const int nr = (pl->g.ny > 1 ? 2 : 0) + (pl->g.nz > 1 && pl->g.zlink ? 2 : 0);
   const int64_t ntiles = (pl->g.N + TV - 1) / TV;
-  const int64_t T = ntiles * pl->Q;
-  int64_t grid = (int64_t)sm_count() * bpsm_for(pl->R, nr) * std::max(1, pl->waves);
+  const int Q = pl->Q;
+  int64_t g0 = (int64_t)sm_count() * bpsm_for(pl->R, nr) * std::max(1, pl->waves);
   if (const char* env = getenv("SSM_LOWRANK_GRID")) {   // launch-shape override for sweeps
     const long v = atol(env);
-    if (v >= 1 && v <= 65536) grid = v;
+    if (v >= 1 && v <= 65536) g0 = v;
   }
-  return std::max<int64_t>(1, std::min(grid, (T + 2 * QC - 1) / (2 * QC)));
+  const int smax = std::max(1, std::min(64, Q / (2 * QC)));   // at least two stages a unit
+  int best = 1;
+  int64_t cost = INT64_MAX;
+  for (int sg = 1; sg <= smax; ++sg) {
+    const int64_t rounds = (ntiles * sg + g0 - 1) / g0;
+    const int64_t c = rounds * ((Q + sg - 1) / sg + kUnitRows);
+    if (c < cost) {
+      cost = c;
+      best = sg;
+    }
+  }
+  *nseg = best;
+  *grid = std::max<int64_t>(1, std::min<int64_t>(g0, ntiles * best));
 }
 
-// segment slots per tile: a tile's rows are shared by at most ceil(G/ntiles) + 1 CTAs
-int lowrank_maxseg(const ssm_plan_s* pl, int64_t grid) {
-  const int64_t ntiles = (pl->g.N + TV - 1) / TV;
-  return (int)((grid + ntiles - 1) / ntiles + 1);
+}  // namespace
+
+int64_t lowrank_grid(const ssm_plan_s* pl) {
+  int64_t grid;
+  int nseg;
+  layout(pl, &grid, &nseg);
+  return grid;
 }
 
 int64_t lowrank_partial_floats(const ssm_plan_s* pl, int64_t grid) {
+  (void)grid;
+  int64_t g;
+  int nseg;
+  layout(pl, &g, &nseg);
   const int64_t ntiles = (pl->g.N + TV - 1) / TV;
-  return ntiles * lowrank_maxseg(pl, grid) * (int64_t)pl->R * TV;
+  return ntiles * nseg * (int64_t)pl->R * TV;
 }
 
 int lowrank_max_partials(const ssm_plan_s* pl) { return (int)lowrank_grid(pl); }
@@ -435,7 +462,13 @@ ssm_status lowrank_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, 
                              int* nparts, cudaStream_t s) {
   LowrankMaps maps;
   SSM_TRY(build_maps(pl, cur, &maps));
-  const int64_t grid = pl->lr_grid;
+  int64_t grid;
+  int nseg;
+  layout(pl, &grid, &nseg);
+  if (grid != pl->lr_grid) {
+    set_error("low-rank form: launch layout changed since planning");
+    return SSM_ECUDA;
+  }
   LowrankArgs a;
   a.Zout = pl->Z[cur ^ 1];
   a.Dout = pl->Dl[cur ^ 1];
@@ -443,8 +476,7 @@ ssm_status lowrank_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, 
   a.Pin = pl->U[cur];
   a.Pout = pl->U[cur ^ 1];
   a.ntiles = (pl->g.N + TV - 1) / TV;
-  a.T = a.ntiles * pl->Q;
-  a.maxseg = lowrank_maxseg(pl, grid);
+  a.nseg = nseg;
   a.coefA = pl->coefA;
   a.coefW = pl->coefW;
   a.partial = partial;
