@@ -228,21 +228,30 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
       // slots of the previous iteration in segment order
       const int nseg = a.nseg;
       float2 av[R / 2];
+      {
+        // slot by slot, all R loads of a slot in flight together (each u_i still sums
+        // the slots in segment order)
+        float us[R];
 #pragma unroll
-      for (int i = 0; i < R / 2; ++i) {
-        float a0 = 0.f, a1 = 0.f;
+        for (int i = 0; i < R; ++i) us[i] = 0.f;
         if (in) {
-          float u0 = 0.f, u1 = 0.f;
-          const float* pt = a.Pin + (tile * nseg) * (int64_t)(R * TV);
+          const float* pt = a.Pin + (tile * nseg) * (int64_t)(R * TV) + v;
           for (int sg = 0; sg < nseg; ++sg) {
-            u0 += pt[(sg * R + 2 * i) * TV + v];
-            u1 += pt[(sg * R + 2 * i + 1) * TV + v];
+#pragma unroll
+            for (int i = 0; i < R; ++i) us[i] += pt[(sg * R + i) * TV];
           }
-          a0 = __ldg(a.S + (2 * i) * ld + n) * __ldg(a.coefA + 2 * i) - __ldg(a.coefW + 2 * i) * u0;
-          a1 = __ldg(a.S + (2 * i + 1) * ld + n) * __ldg(a.coefA + 2 * i + 1) -
-               __ldg(a.coefW + 2 * i + 1) * u1;
         }
-        av[i] = make_float2(a0, a1);
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+          float a0 = 0.f, a1 = 0.f;
+          if (in) {
+            a0 = __ldg(a.S + (2 * i) * ld + n) * __ldg(a.coefA + 2 * i) -
+                 __ldg(a.coefW + 2 * i) * us[2 * i];
+            a1 = __ldg(a.S + (2 * i + 1) * ld + n) * __ldg(a.coefA + 2 * i + 1) -
+                 __ldg(a.coefW + 2 * i + 1) * us[2 * i + 1];
+          }
+          av[i] = make_float2(a0, a1);
+        }
       }
       float2 uacc[R / 2];
 #pragma unroll
