@@ -126,13 +126,25 @@ __global__ void __launch_bounds__(VT * WPB, min_blocks<R>())
 
   // a_i = S_i/(beta + sigma_{c,i}^2) - W_{c,i} u_i, u summed over the tile's segments of
   // the previous iteration in segment order
-  for (int i = warp; i < R; i += WPB) {
-    float u = 0.f;
-    const float* pt = Uin + (tile * nseg) * (int64_t)(R * VT) + i * VT + lane;
-    for (int k = 0; k < nseg; ++k) u += pt[(int64_t)k * R * VT];
-    sh_a[i][lane] = in ? P.S[(int64_t)i * ld + n] * __ldg(P.coefA + c * R + i) -
-                             __ldg(P.coefW + c * R + i) * u
-                       : 0.f;
+  {
+    // this warp's ranks i = warp + j WPB; slot by slot, their loads in flight together
+    constexpr int RPW = R / WPB;
+    static_assert(R % WPB == 0, "ranks are padded to a multiple of the warps per block");
+    float us[RPW];
+#pragma unroll
+    for (int j = 0; j < RPW; ++j) us[j] = 0.f;
+    const float* pt = Uin + (tile * nseg) * (int64_t)(R * VT) + warp * VT + lane;
+    for (int k = 0; k < nseg; ++k) {
+#pragma unroll
+      for (int j = 0; j < RPW; ++j) us[j] += pt[((int64_t)k * R + j * WPB) * VT];
+    }
+#pragma unroll
+    for (int j = 0; j < RPW; ++j) {
+      const int i = warp + j * WPB;
+      sh_a[i][lane] = in ? P.S[(int64_t)i * ld + n] * __ldg(P.coefA + c * R + i) -
+                               __ldg(P.coefW + c * R + i) * us[j]
+                         : 0.f;
+    }
   }
   __syncthreads();
   float2 av[R / 2];
