@@ -1,4 +1,4 @@
-// FP64 power iteration for the largest eigenvalue of the Hessian of Eq. 7,
+// FP64 iterations on the device for the largest eigenvalue of the Hessian of Eq. 7,
 //
 //     H = I_N (x) K^T K + lambda D^T D (x) I_Q      (acting on the Q x N compartment maps),
 //
@@ -9,19 +9,25 @@
 // H is a Kronecker sum, so its eigenvalues are mu_i + lambda nu_j (mu_i those of K^T K,
 // nu_j those of D^T D) and lambda_max(H) = lambda_max(K^T K) + lambda lambda_max(D^T D).
 // On the free-boundary box grid, D^T D = s (L_x (+) L_y (+) L_z) is again a Kronecker sum,
-// of path-graph Laplacians, one per axis. Each factor gets its own FP64 power iteration on
-// the device, all in one launch:
-//   block 0           K^T K through the plan's FP64 Gram matrix of the smaller side
-//                     (K K^T has the same nonzero spectrum); one warp per matrix row
-//   blocks 1 .. naxes s L_path of one grid axis with >= 2 voxels; one warp, the two
-//                     vectors in shared memory
+// of path-graph Laplacians, one per axis. Each factor gets its own FP64 iteration:
+//   K^T K    power iteration on the plan's FP64 Gram matrix of the smaller side (K K^T has
+//            the same nonzero spectrum). A step is a matrix-vector product spread over
+//            the device (a warp per row) and a one-block normalisation; the host tests
+//            the stopping rule every 32 steps.
+//   s L_path power iteration on (sigma I - s L)^{-1} with sigma = 4 s (inverse iteration;
+//            sigma lies above the path Laplacian's spectrum, whose largest eigenvalue is
+//            s (2 + 2 cos(pi/n)) < 4 s). Its iterates converge to the same eigenvector as
+//            plain power iteration on s L, but contract by about 1/4 per step instead of
+//            1 - O(1/n^2): ~15 steps instead of tens of thousands for a 192-voxel axis.
+//            A step is one tridiagonal solve (Thomas algorithm, one thread per axis).
 // The start vectors are fixed pseudo-random values (a counter-based hash of the index).
-// The Rayleigh quotient x^T A x of the normalised power iterates of a symmetric positive
-// semidefinite A never decreases; an iteration stops once 32 further steps have raised it
-// by at most 1e-15 of its value, or at its cap, where it is reported as not converged
-// (the value is then a lower bound of the eigenvalue).
+// The Rayleigh quotient x^T A x / x^T x of the iterates (with A = K^T K, or s L itself)
+// does not decrease; an iteration stops once it rises by at most 1e-15 of its value over
+// a test interval (32 steps for the Gram factor, one for the axes), or at its cap, where
+// it is reported as not converged (the value is then a lower bound of the eigenvalue).
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "ssm_internal.cuh"
 
@@ -29,8 +35,10 @@ namespace ssm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kCheck = 32;                 // steps between stopping tests
-constexpr int kMaxAxis = 8192;             // longest axis iterated (shared memory)
+constexpr int kCheck = 32;                 // Gram steps between stopping tests
+constexpr int kGramCap = 4096;             // Gram steps at most
+constexpr int kAxisCap = 200;              // inverse-iteration steps at most
+constexpr int64_t kMaxAxis = (int64_t)1 << 22;   // longest axis iterated
 
 // splitmix64 of (i, salt) mapped to [0.5, 1.5): start vectors with no special structure
 __device__ __forceinline__ double start_value(int64_t i, int salt) {
@@ -46,13 +54,7 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-struct PowerOut {
-  double value[4];     // [0] K^T K, [1..3] s L of axis 0..2
-  int iters[4];
-  int converged[4];
-};
-
-// block-wide sums of two values (kThreads threads)
+// block-wide sums of two values (kThreads threads), the same order every call
 __device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[2]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   a = warp_sum(a);
@@ -72,10 +74,15 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[2
   __syncthreads();
 }
 
-__device__ void power_gram(const double* __restrict__ A, int n, double* __restrict__ x,
-                           double* __restrict__ y, int max_iter, PowerOut* out) {
+struct PowerOut {
+  double value[4];     // [0] K^T K, [1..3] s L of axis 0..2
+  int iters[4];
+  int converged[4];
+};
+
+// x = start vector / its norm (one block)
+__global__ void __launch_bounds__(kThreads) gram_start_kernel(double* __restrict__ x, int n) {
   __shared__ double red[kThreads / 32][2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double xx = 0.0, dummy = 0.0;
   for (int i = threadIdx.x; i < n; i += kThreads) {
     const double v = start_value(i, 0);
@@ -83,154 +90,127 @@ __device__ void power_gram(const double* __restrict__ A, int n, double* __restri
     xx += v * v;
   }
   block_sum2(xx, dummy, red);
-  const double inv0 = 1.0 / sqrt(xx);
-  for (int i = threadIdx.x; i < n; i += kThreads) x[i] *= inv0;
-  __syncthreads();
-  double rq = 0.0, rq_ref = -1.0;
-  int k = 0, conv = 0;
-  while (k < max_iter) {
-    // y = A x: one warp per row, lanes stride the columns (coalesced rows of A)
-    for (int i = warp; i < n; i += kThreads / 32) {
-      const double* row = A + (int64_t)i * n;
-      double acc = 0.0;
-      for (int j = lane; j < n; j += 32) acc = fma(row[j], x[j], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) y[i] = acc;
-    }
-    __syncthreads();
-    double xy = 0.0, yy = 0.0;
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-      xy = fma(x[i], y[i], xy);
-      yy = fma(y[i], y[i], yy);
-    }
-    block_sum2(xy, yy, red);
-    rq = xy;                               // x has unit norm
-    ++k;
-    if (!(yy > 0.0)) break;                // A x = 0: the largest eigenvalue is 0
-    const double inv = 1.0 / sqrt(yy);
-    for (int i = threadIdx.x; i < n; i += kThreads) x[i] = y[i] * inv;
-    __syncthreads();
-    if (k % kCheck == 0) {
-      if (rq_ref >= 0.0 && rq - rq_ref <= 1e-15 * fabs(rq)) {
-        conv = 1;
-        break;
-      }
-      rq_ref = rq;
-    }
-  }
-  if (threadIdx.x == 0) {
-    out->value[0] = rq;
-    out->iters[0] = k;
-    out->converged[0] = conv || !(rq > 0.0);
+  const double inv = 1.0 / sqrt(xx);
+  for (int i = threadIdx.x; i < n; i += kThreads) x[i] *= inv;
+}
+
+// y = A x, a warp per row (rows grid-strided), lanes striding the columns (coalesced)
+__global__ void __launch_bounds__(kThreads) gram_matvec_kernel(const double* __restrict__ A,
+                                                               int n,
+                                                               const double* __restrict__ x,
+                                                               double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+  for (int64_t i = blockIdx.x * (int64_t)(kThreads / 32) + (threadIdx.x >> 5); i < n; i += warps) {
+    const double* row = A + i * n;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc = fma(row[j], x[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[i] = acc;
   }
 }
 
-// one warp: s L_path of length n (free boundary), vectors in shared memory. The iterate
-// is normalised only every kCheck steps, where the Rayleigh quotient is formed: ||s L||
-// <= 4 s <= 8 bounds the growth in between by 8^kCheck = 2^96, far inside FP64's range,
-// and the eigenvalue is at least s (so the iterate does not shrink). A step is then one
-// stencil pass, without the two warp reductions, the square root and the division of a
-// normalised step (32-voxel axes: ~2k steps; 128: ~35k).
-__device__ void power_axis(int n, double s, int axis, int max_iter, double* x, double* y,
-                           PowerOut* out) {
-  const int lane = threadIdx.x;
-  double xx = 0.0;
-  for (int i = lane; i < n; i += 32) {
-    const double v = start_value(i, 1 + axis);
-    x[i] = v;
-    xx += v * v;
+// rq[step] = x^T y (x has unit norm, y = A x); x = y / ||y|| (one block). A zero y
+// (A x = 0: the largest eigenvalue is 0) records rq = 0 and leaves x alone.
+__global__ void __launch_bounds__(kThreads) gram_normalise_kernel(double* __restrict__ x,
+                                                                  const double* __restrict__ y,
+                                                                  int n, double* __restrict__ rq,
+                                                                  int step) {
+  __shared__ double red[kThreads / 32][2];
+  double xy = 0.0, yy = 0.0;
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    xy = fma(x[i], y[i], xy);
+    yy = fma(y[i], y[i], yy);
   }
-  xx = warp_sum(xx);
-  const double inv0 = 1.0 / sqrt(xx);
-  for (int i = lane; i < n; i += 32) x[i] *= inv0;
-  __syncwarp();
-  double rq = 0.0, rq_ref = -1.0;
-  int k = 0, conv = 0;
-  while (k < max_iter) {
-    // kCheck - 1 plain steps: y = s L x, then swap
-    for (int t = 1; t < kCheck && k < max_iter; ++t, ++k) {
-      for (int i = lane; i < n; i += 32) {
-        const double xi = x[i];
-        double v = 0.0;
-        if (i > 0) v += xi - x[i - 1];
-        if (i < n - 1) v += xi - x[i + 1];
-        y[i] = v * s;
-      }
-      __syncwarp();
-      double* tmp = x;
-      x = y;
-      y = tmp;
-    }
-    if (k >= max_iter) break;
-    // the last step of the block forms x^T (s L) x / x^T x and normalises
-    double xy = 0.0, yy = 0.0, xn = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      const double xi = x[i];
-      double v = 0.0;
-      if (i > 0) v += xi - x[i - 1];
-      if (i < n - 1) v += xi - x[i + 1];
-      v *= s;
-      y[i] = v;
-      xy = fma(xi, v, xy);
-      yy = fma(v, v, yy);
-      xn = fma(xi, xi, xn);
-    }
-    xy = warp_sum(xy);
-    yy = warp_sum(yy);
-    xn = warp_sum(xn);
-    ++k;
-    if (!(yy > 0.0) || !(xn > 0.0)) break;
-    rq = xy / xn;
-    const double inv = 1.0 / sqrt(yy);
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) x[i] = y[i] * inv;
-    __syncwarp();
-    if (rq_ref >= 0.0 && rq - rq_ref <= 1e-15 * fabs(rq)) {
-      conv = 1;
-      break;
-    }
-    rq_ref = rq;
-  }
-  if (lane == 0) {
-    out->value[1 + axis] = rq;
-    out->iters[1 + axis] = k;
-    out->converged[1 + axis] = conv;
-  }
+  block_sum2(xy, yy, red);
+  if (threadIdx.x == 0) rq[step] = yy > 0.0 ? xy : 0.0;
+  if (!(yy > 0.0)) return;
+  const double inv = 1.0 / sqrt(yy);
+  for (int i = threadIdx.x; i < n; i += kThreads) x[i] = y[i] * inv;
 }
 
 struct AxisSet {
   int len[3];
-  int axis[3];     // which grid axis each iterated block handles
-  int cap[3];      // iteration cap of each
+  int axis[3];       // which grid axis each entry is
+  int64_t base[3];   // offset of its scratch (4 arrays of len doubles)
   int count;
 };
 
-__global__ void __launch_bounds__(kThreads) power_kernel(const double* __restrict__ A, int n,
-                                                         double* __restrict__ xg,
-                                                         double* __restrict__ yg, AxisSet axes,
-                                                         double s, int max_gram,
-                                                         PowerOut* out) {
-  extern __shared__ double sh[];
-  if (blockIdx.x == 0) {
-    power_gram(A, n, xg, yg, max_gram, out);
-    return;
+// one thread per axis: inverse iteration x <- (sigma I - s L)^{-1} x, sigma = 4 s, on the
+// path of n voxels with the free boundary (diagonal of s L: s deg, off-diagonals -s).
+// The tridiagonal system is factored once (Thomas: cp = modified super-diagonal,
+// im = reciprocal pivots) and each step is one forward and one backward sweep; the
+// Rayleigh quotient is formed with s L itself.
+__global__ void axis_inverse_kernel(AxisSet axes, double s, double* __restrict__ scratch,
+                                    PowerOut* __restrict__ out) {
+  const int b = blockIdx.x;
+  if (b >= axes.count || threadIdx.x != 0) return;
+  const int n = axes.len[b];
+  double* x = scratch + axes.base[b];
+  double* y = x + n;
+  double* cp = y + n;
+  double* im = cp + n;
+  const double sigma = 4.0 * s, e = s;   // sigma I - s L: off-diagonals +s
+  auto diag = [&](int i) { return sigma - s * (double)((i > 0) + (i < n - 1)); };
+  // factor
+  double m = diag(0);
+  im[0] = 1.0 / m;
+  cp[0] = e / m;
+  for (int i = 1; i < n; ++i) {
+    m = diag(i) - e * cp[i - 1];
+    im[i] = 1.0 / m;
+    cp[i] = e / m;
   }
-  const int b = blockIdx.x - 1;
-  if (b >= axes.count || threadIdx.x >= 32) return;
-  const int len = axes.len[b];
-  power_axis(len, s, axes.axis[b], axes.cap[b], sh, sh + len, out);
+  // start vector, unit norm
+  double xx = 0.0;
+  for (int i = 0; i < n; ++i) {
+    x[i] = start_value(i, 1 + axes.axis[b]);
+    xx += x[i] * x[i];
+  }
+  double inv = 1.0 / sqrt(xx);
+  for (int i = 0; i < n; ++i) x[i] *= inv;
+  double rq = 0.0, rq_prev = -1.0;
+  int k = 0, conv = 0;
+  while (k < kAxisCap) {
+    // solve (sigma I - s L) y = x: forward sweep into y, backward in place
+    y[0] = x[0] * im[0];
+    for (int i = 1; i < n; ++i) y[i] = (x[i] - e * y[i - 1]) * im[i];
+    for (int i = n - 2; i >= 0; --i) y[i] -= cp[i] * y[i + 1];
+    ++k;
+    // Rayleigh quotient of s L at y, and y / ||y|| as the next iterate
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double ly = 0.0;
+      if (i > 0) ly += y[i] - y[i - 1];
+      if (i < n - 1) ly += y[i] - y[i + 1];
+      num = fma(y[i], s * ly, num);
+      den = fma(y[i], y[i], den);
+    }
+    if (!(den > 0.0)) break;
+    rq = num / den;
+    inv = 1.0 / sqrt(den);
+    for (int i = 0; i < n; ++i) x[i] = y[i] * inv;
+    if (rq_prev >= 0.0 && rq - rq_prev <= 1e-15 * fabs(rq)) {
+      conv = 1;
+      break;
+    }
+    rq_prev = rq;
+  }
+  out->value[1 + axes.axis[b]] = rq;
+  out->iters[1 + axes.axis[b]] = k;
+  out->converged[1 + axes.axis[b]] = conv;
 }
 
 }  // namespace
 
 // lambda_max of K^T K (from the Gram matrix A, n x n, of the smaller side; A is read, not
-// modified) and of D^T D on the plan's box grid, each by power iteration; stored in the
-// plan (pl->kk_power, pl->dtd_power, pl->hess_power, pl->power_iters, pl->power_conv).
-// Synchronises `s`.
+// modified) and of D^T D on the plan's box grid; stored in the plan (pl->kk_power,
+// pl->dtd_power, pl->hess_power, pl->power_iters, pl->power_conv). Synchronises `s`.
 ssm_status hessian_power(ssm_plan_s* pl, const double* A, int n, cudaStream_t s) {
   AxisSet axes{};
   const int naxes = pl->g.zlink ? pl->p.ndim : std::min(pl->p.ndim, 2);
   bool skipped_axis = false;
+  int64_t scratch_len = 0;
   for (int d = 0; d < naxes; ++d) {
     const int64_t len = pl->p.dims[d];
     if (len < 2) continue;
@@ -241,43 +221,80 @@ ssm_status hessian_power(ssm_plan_s* pl, const double* A, int n, cudaStream_t s)
     }
     axes.len[axes.count] = (int)len;
     axes.axis[axes.count] = d;
-    // an axis of n voxels contracts by about 1 - (pi/n)^2 per step (~25k steps for 128
-    // voxels, ~100k for 256); the cap bounds each axis to 2^25 element updates
-    axes.cap[axes.count] = (int)std::min<int64_t>(262144, ((int64_t)1 << 25) / len);
+    axes.base[axes.count] = scratch_len;
+    scratch_len += 4 * len;
     ++axes.count;
   }
-  int maxlen = 0;
-  for (int i = 0; i < axes.count; ++i) maxlen = std::max(maxlen, axes.len[i]);
   double* buf = nullptr;
-  const size_t nbuf = (size_t)2 * n + (sizeof(PowerOut) + 7) / 8;
+  // Gram x, y and the Rayleigh quotients; the axes' scratch; the result record
+  const size_t nbuf = (size_t)2 * n + kGramCap + (size_t)scratch_len + (sizeof(PowerOut) + 7) / 8;
   SSM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&buf), sizeof(double) * nbuf, s));
-  PowerOut* dout = reinterpret_cast<PowerOut*>(buf + 2 * n);
-  SSM_CUDA(cudaMemsetAsync(dout, 0, sizeof(PowerOut), s));
-  const size_t shm = sizeof(double) * 2 * (size_t)std::max(maxlen, 1);
-  if (shm > 48 * 1024)
-    SSM_CUDA(cudaFuncSetAttribute(power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)shm));
+  double* gx = buf;
+  double* gy = gx + n;
+  double* rq = gy + n;
+  double* ax = rq + kGramCap;
+  PowerOut* dout = reinterpret_cast<PowerOut*>(ax + scratch_len);
+  auto fail = [&](ssm_status st) {
+    cudaFreeAsync(buf, s);
+    return st;
+  };
+  if (cudaMemsetAsync(dout, 0, sizeof(PowerOut), s) != cudaSuccess) return fail(SSM_ECUDA);
   const double sc = pl->p.stencil_pairs == 2 ? 2.0 : 1.0;
-  // the Gram iteration contracts by (sigma_2/sigma_1)^2 per step
-  power_kernel<<<1 + axes.count, kThreads, shm, s>>>(A, n, buf, buf + n, axes, sc, 4096, dout);
+  if (axes.count > 0) {
+    axis_inverse_kernel<<<axes.count, 32, 0, s>>>(axes, sc, ax, dout);
+    SSM_LAUNCHED();
+  }
+  // Gram factor: blocks of kCheck steps, the stopping rule tested on the host between
+  // blocks (the contraction per step is (sigma_2 / sigma_1)^2)
+  gram_start_kernel<<<1, kThreads, 0, s>>>(gx, n);
   SSM_LAUNCHED();
+  const unsigned mv_grid = (unsigned)std::max(1, std::min(4 * sm_count(), (n + 7) / 8));
+  int k = 0, conv = 0;
+  double kk = 0.0, ref = -1.0;
+  std::vector<double> hrq(kCheck);
+  while (k < kGramCap) {
+    const int steps = std::min(kCheck, kGramCap - k);
+    for (int t = 0; t < steps; ++t) {
+      gram_matvec_kernel<<<mv_grid, kThreads, 0, s>>>(A, n, gx, gy);
+      SSM_LAUNCHED();
+      gram_normalise_kernel<<<1, kThreads, 0, s>>>(gx, gy, n, rq, k + t);
+      SSM_LAUNCHED();
+    }
+    if (cudaMemcpyAsync(hrq.data(), rq + k, sizeof(double) * steps, cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(SSM_ECUDA);
+    k += steps;
+    kk = hrq[steps - 1];
+    if (!(kk > 0.0)) {            // A x = 0
+      kk = 0.0;
+      conv = 1;
+      break;
+    }
+    if (ref >= 0.0 && kk - ref <= 1e-15 * std::fabs(kk)) {
+      conv = 1;
+      break;
+    }
+    ref = kk;
+  }
   PowerOut h{};
-  SSM_CUDA(cudaMemcpyAsync(&h, dout, sizeof(PowerOut), cudaMemcpyDeviceToHost, s));
+  if (cudaMemcpyAsync(&h, dout, sizeof(PowerOut), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(SSM_ECUDA);
   SSM_CUDA(cudaFreeAsync(buf, s));
-  SSM_CUDA(cudaStreamSynchronize(s));
-  pl->kk_power = h.value[0];
+  pl->kk_power = kk;
   double dtd = 0.0;
-  int iters = h.iters[0];
-  bool conv = h.converged[0] != 0 && !skipped_axis;
+  int iters = k;
+  bool ok = conv != 0 && !skipped_axis;
   for (int i = 0; i < axes.count; ++i) {
     dtd += h.value[1 + axes.axis[i]];
     iters = std::max(iters, h.iters[1 + axes.axis[i]]);
-    conv = conv && h.converged[1 + axes.axis[i]] != 0;
+    ok = ok && h.converged[1 + axes.axis[i]] != 0;
   }
   pl->dtd_power = dtd;
   pl->hess_power = pl->kk_power + pl->p.lambda * dtd;
   pl->power_iters = iters;
-  pl->power_conv = conv ? 1 : 0;
+  pl->power_conv = ok ? 1 : 0;
   return SSM_OK;
 }
 

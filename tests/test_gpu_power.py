@@ -1,4 +1,5 @@
-"""The FP64 device power iteration for lambda_max of the Hessian of Eq. 7 (ssm_plan).
+"""The FP64 device iterations for lambda_max of the Hessian of Eq. 7 (ssm_plan): power
+iteration on the Gram factor, inverse iteration on the grid axes.
 
 H = I_N (x) K^T K + lambda D^T D (x) I_Q bounds the step of a gradient method on Eq. 7;
 xi_p of Eq. 32 is to exceed 0.75 lambda ||D^T D|| (the convergence condition cited in
@@ -72,7 +73,23 @@ def test_full_size_plans(name):
     kk, dtd, hess = closed_form(K, w.dims, w.lam, 2)
     assert info["power_converged"] == 1, info
     assert info["kk_norm"] == pytest.approx(kk, rel=1e-10)
-    # an axis of n voxels converges like 1 - (pi/n)^2 per step: the stopping rule leaves
-    # well under 1e-10 relative on 64..192-voxel axes
+    # the axes run inverse iteration (about a factor 4 per step): the stopping rule
+    # leaves well under 1e-10 relative
     assert info["dtd_norm_power"] == pytest.approx(dtd, rel=1e-10)
+    assert info["power_iters"] <= 4096
+
+
+@pytest.mark.parametrize("dims", [(6000,), (3000, 3), (2, 2), (2,)])
+def test_long_and_short_axes(dims):
+    """Inverse iteration on axes far longer than a power iteration could resolve in its
+    budget (plain power iteration contracts like 1 - (pi/n)^2 per step), and the
+    shortest ones."""
+    K, _, _ = synth.random_problem(6, 9, (1, 1), seed=4)
+    plan = ssm.Plan(K, dims, 0.3, 1.0, form="lowrank", max_iter=1)
+    info = plan.info()
+    plan.close()
+    kk, dtd, hess = closed_form(K, dims, 0.3, 2)
+    assert info["power_converged"] == 1, info
+    assert info["dtd_norm_power"] == pytest.approx(dtd, rel=1e-10)
+    assert info["hess_norm"] == pytest.approx(hess, rel=1e-10)
     assert info["hess_norm"] == pytest.approx(hess, rel=1e-10)
