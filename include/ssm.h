@@ -114,17 +114,19 @@ typedef struct {
    * 0.75 lambda ||D^T D|| (the convergence condition the paper cites, Sec. III-C). H is
    * a Kronecker sum, so lambda_max(H) = lambda_max(K^T K) + lambda lambda_max(D^T D),
    * and D^T D on the box grid is a Kronecker sum of path-graph Laplacians; ssm_plan runs
-   * one FP64 power iteration on the device per factor (K^T K via the Gram matrix of the
-   * smaller side; one per grid axis of 2 .. 8192 voxels). With a mask the grid values
-   * are the box grid's (an upper bound of the masked operator's).                     */
+   * one FP64 iteration on the device per factor: power iteration on the Gram matrix of
+   * the smaller side for K^T K, and power iteration on (4 s I - s L)^{-1} (inverse
+   * iteration) for each grid axis of 2 .. 2^22 voxels. With a mask the grid values are
+   * the box grid's (an upper bound of the masked operator's).                          */
   double hess_norm;        /* lambda_max(K^T K) + lambda lambda_max(D^T D)           */
   double kk_norm;          /* lambda_max(K^T K) by power iteration (sigma_1^2)       */
   double dtd_norm_power;   /* lambda_max(D^T D) by power iteration                   */
-  int power_iters;         /* most steps any of the power iterations took            */
-  int power_converged;     /* 1: every power iteration met its stopping rule (an
-                              increase of at most 1e-15 relative over 32 steps); 0:
-                              one hit its cap (its value is a lower bound) or an axis
-                              longer than 8192 voxels was left out                  */
+  int power_iters;         /* most steps any of the iterations took                 */
+  int power_converged;     /* 1: every iteration met its stopping rule (its Rayleigh
+                              quotient rose by at most 1e-15 relative over 32 steps
+                              for K^T K, over one step for an axis); 0: one hit its
+                              cap (its value is a lower bound) or an axis longer
+                              than 2^22 voxels was left out                          */
 } ssm_info;
 
 /* Fill `p` with defaults: 2D, lambda 0, beta 1, xi_p rule, low-rank auto rank,
