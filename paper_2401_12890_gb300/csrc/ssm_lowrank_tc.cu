@@ -129,6 +129,8 @@ struct LrtcMaps {
   CUtensorMap v1h, v1l;   // V (Q x RP), box {32, QC}, 128-byte swizzle
   CUtensorMap v2h, v2l;   // V^T (RP x Qs), box {QC, RP}, 128-byte swizzle
   CUtensorMap zc, zn;     // z^k (Q x N), boxes {ZW, QC} and {NW, QC}
+  CUtensorMap dd;         // d^k (Q x N), box {TV, QC}: prefetched into L2 before a residual
+                          // test reads it
 };
 
 struct LrtcArgs {
@@ -340,6 +342,7 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
       tma_prefetch_map(&maps.zn);
       tma_prefetch_map(&maps.v1h);
       tma_prefetch_map(&maps.v2h);
+      if (CHECK) tma_prefetch_map(&maps.dd);
       int g = 0;
       int64_t tile;
       int c0, c1, sg;
@@ -350,9 +353,16 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
         // staged loads and the neighbour rows, which other CTAs prefetched, hit L2)
         for (int c = c0 + 1; c < c0 + kPrefetch && c < c1; ++c)
           tma_prefetch_2d(&maps.zc, (int)(n0 - 4), c * QC);
+        // a residual test also reads d^k, element by element in the epilogue: its rows
+        // are prefetched into L2 the same way (the first kPrefetch chunks at once)
+        if (CHECK)
+          for (int c = c0; c < c0 + kPrefetch && c < c1; ++c)
+            tma_prefetch_2d(&maps.dd, (int)n0, c * QC);
         for (int c = c0; c < c1; ++c, ++g) {
           const int q0 = c * QC;
           if (c + kPrefetch < c1) tma_prefetch_2d(&maps.zc, (int)(n0 - 4), q0 + kPrefetch * QC);
+          if (CHECK && c + kPrefetch < c1)
+            tma_prefetch_2d(&maps.dd, (int)n0, q0 + kPrefetch * QC);
           // the chunk's V boxes (product 1 needs them first)
           const int sv = g % NSV, kv = g / NSV;
           if (kv > 0 && !mbar_wait_sleep(&vempty[sv], (kv - 1) & 1)) {
@@ -573,6 +583,16 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
       for (int i = 0; i < nchk; ++i) {
         const int gg = g + i, sz = gg % NSZ, b = gg % NVA, p = gg & 1;
         const int qg = (c0 + i) * QC + grp * GC;   // this warp's first compartment
+        // a residual test needs d^k, read from global memory element by element: the
+        // chunk's loads are issued before the waits, so that their latency overlaps the
+        // chunk's processing (loading them where they are used cost 2.7x per iteration)
+        float dkc[CHECK ? GC : 1];
+        if constexpr (CHECK) {
+          const int jn0 = min(GC, Q - qg);
+          const float* dq = a.Din + (int64_t)qg * ld + n;
+#pragma unroll
+          for (int j = 0; j < GC; ++j) dkc[j] = (in && j < jn0) ? __ldg(dq + j * ld) : 0.f;
+        }
         if (!failed && !mbar_wait_sleep(&zfull[sz], (gg / NSZ) & 1)) failed = true;
         if (!failed && !mbar_wait_sleep(&va_full[b], (gg / NVA) & 1)) failed = true;
         fence_after();
@@ -623,14 +643,10 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
             }
             if constexpr (CHECK) {
               // f^{k+1} = t - d^k / beta needs d^k
-              float dk[8];
-#pragma unroll
-              for (int j = 0; j < 8; ++j)
-                dk[j] = h + j < jn ? __ldg(a.Din + (zp - a.Zout) + (h + j) * ld) : 0.f;
 #pragma unroll
               for (int j = 0; j < 8; ++j)
                 if (h + j < jn) {
-                  const float f = tt[j] - dk[j] * inv_beta;
+                  const float f = tt[j] - dkc[h + j] * inv_beta;
                   const float e = zn[j] - f, ch = zn[j] - zz[j];
                   s1 = fmaf(e, e, s1);
                   s2 = fmaf(ch, ch, s2);
@@ -893,6 +909,7 @@ ssm_status lrtc_iteration(ssm_plan_s* pl, int cur, bool check, bool write_d, dou
   SSM_CUDA(encode_2d(&m.v2l, F32, 4, pl->V2l, Q, RP, Qs, QC, (unsigned)RP, SW));
   SSM_CUDA(encode_2d(&m.zc, F32, 4, pl->Z[cur], N, Q, ld, ZW, QC));
   SSM_CUDA(encode_2d(&m.zn, F32, 4, pl->Z[cur], N, Q, ld, NW, QC));
+  SSM_CUDA(encode_2d(&m.dd, F32, 4, pl->Dl[cur], N, Q, ld, TV, QC));
   int64_t grid;
   int spc, split;
   layout(pl, &grid, &spc, &split);
