@@ -198,19 +198,6 @@ __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 8 consecutive 32-bit TMEM columns of this warp's 32 lanes (one lane per thread)
-__device__ __forceinline__ void tld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tst8(uint32_t taddr, const float* v) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(
@@ -222,6 +209,55 @@ __device__ __forceinline__ void tst8(uint32_t taddr, const float* v) {
 }
 __device__ __forceinline__ void tst_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// C consecutive 32-bit columns at each of two TMEM addresses (one lane per thread): both
+// loads are in flight together and one wait covers them (the outputs are defined by the
+// statement that waits, so no use of them can be scheduled before the wait)
+template <int C>
+__device__ __forceinline__ void tld2(uint32_t t0, uint32_t t1, float* v0, float* v1) {
+  static_assert(C == 8 || C == 16, "columns per load");
+  uint32_t r[2 * C];
+  if constexpr (C == 8) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(t0), "r"(t1)
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, "
+        "%25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(t0), "r"(t1)
+        : "memory");
+  }
+#pragma unroll
+  for (int i = 0; i < C; ++i) {
+    v0[i] = __uint_as_float(r[i]);
+    v1[i] = __uint_as_float(r[C + i]);
+  }
+}
+
+// C columns (a multiple of 8) at each of two TMEM addresses, 16 (or 8) per wait
+template <int C>
+__device__ __forceinline__ void tld2_cols(uint32_t t0, uint32_t t1, float* v0, float* v1) {
+  static_assert(C % 8 == 0, "columns");
+  constexpr int S = C % 16 == 0 ? 16 : 8;
+#pragma unroll
+  for (int k = 0; k < C; k += S) tld2<S>(t0 + k, t1 + k, v0 + k, v1 + k);
 }
 
 template <int RP, int NR, bool CHECK, bool WD>
@@ -483,6 +519,8 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
     const float c2 = a.lam_s * a.inv_xb;             // weight of the neighbour sum
     const float c3 = a.beta * a.inv_xb;              // weight of V a
     const float beta = a.beta, inv_beta = a.inv_beta;
+    const float2 c2_2 = make_float2(c2, c2), c3_2 = make_float2(c3, c3);
+    const float2 beta2 = make_float2(beta, beta), two2 = make_float2(2.f, 2.f);
     int g = 0, si = 0;
     int64_t tile;
     int c0, c1, sg;
@@ -513,6 +551,8 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
       // neighbour presence as 0/1 weights: the staged rows are always readable (finite
       // z values or the copy's zero fill), so every neighbour term is a fused add
       const float fxm = hxm ? 1.f : 0.f, fxp = hxp ? 1.f : 0.f;
+      const float2 fxm2 = make_float2(fxm, fxm), fxp2 = make_float2(fxp, fxp);
+      const float2 e1_2 = make_float2(e1, e1);
       int nidx[4];
       float fk[4];
       {
@@ -523,6 +563,9 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
           fk[j] = (j < NR && flags[j]) ? 1.f : 0.f;
         }
       }
+      float2 fk2[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) fk2[j] = make_float2(fk[j], fk[j]);
       // a for this warp's ranks: a_i = S_i/(beta + sigma_i^2) - W_i u_i, u_i summed over
       // the tile's segment slots of the previous iteration in segment order
       if (si > 0 && !failed && !mbar_wait_sleep(a_free, (si - 1) & 1)) failed = true;
@@ -568,13 +611,16 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
         if (!failed && !mbar_wait_sleep(&u_full[p], (gg >> 1) & 1)) failed = true;
         fence_after();
         const uint32_t ub = tmem + lane_base + L::T_U + 2 * RP * (gg % UB) + grp * RQ;
+        {
+          float um[RQ], uc[RQ];
+          tld2_cols<RQ>(ub, ub + RP, um, uc);
 #pragma unroll
-        for (int i = 0; i < RQ; i += 8) {
-          float um[8], uc[8];
-          tld8(ub + i, um);
-          tld8(ub + RP + i, uc);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) uacc[i + j] += um[j] + uc[j];
+          for (int j = 0; j < RQ; j += 2) {
+            const float2 t2 = __fadd2_rn(make_float2(um[j], um[j + 1]), make_float2(uc[j], uc[j + 1]));
+            const float2 s2 = __fadd2_rn(make_float2(uacc[j], uacc[j + 1]), t2);
+            uacc[j] = s2.x;
+            uacc[j + 1] = s2.y;
+          }
         }
         fence_before();
         __syncwarp();
@@ -597,13 +643,16 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
         if (!failed && !mbar_wait_sleep(&va_full[b], (gg / NVA) & 1)) failed = true;
         fence_after();
         float va[GC];
+        {
+          float vc[GC];
+          const uint32_t tb = tmem + lane_base + L::T_VA + 64 * b + grp * GC;
+          tld2_cols<GC>(tb, tb + 32, va, vc);
 #pragma unroll
-        for (int j = 0; j < GC; j += 8) {
-          float vc[8];
-          tld8(tmem + lane_base + L::T_VA + 64 * b + grp * GC + j, va + j);
-          tld8(tmem + lane_base + L::T_VA + 64 * b + 32 + grp * GC + j, vc);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) va[j + k] += vc[k];
+          for (int k = 0; k < GC; k += 2) {
+            const float2 s2 = __fadd2_rn(make_float2(va[k], va[k + 1]), make_float2(vc[k], vc[k + 1]));
+            va[k] = s2.x;
+            va[k + 1] = s2.y;
+          }
         }
         fence_before();
         __syncwarp();
@@ -622,24 +671,42 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
           // arithmetic, then the stores
 #pragma unroll
           for (int h = 0; h < GC; h += 8) {
-            float zz[8], nb[8];
+            // compartments in pairs, in packed FP32x2 arithmetic: each half of an FP32x2
+            // operation rounds as the scalar one, so the values are those of scalar code
+            float2 zz2[4], nb2[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int r = h + j;
-              zz[j] = zcr[r * ZW];
-              nb[j] = fxm * zcr[r * ZW - 1];
-              nb[j] = fmaf(fxp, zcr[r * ZW + 1], nb[j]);
+            for (int j = 0; j < 4; ++j) {
+              const int r = h + 2 * j;
+              zz2[j] = make_float2(zcr[r * ZW], zcr[(r + 1) * ZW]);
+              nb2[j] = __fmul2_rn(fxm2, make_float2(zcr[r * ZW - 1], zcr[(r + 1) * ZW - 1]));
+              nb2[j] = __ffma2_rn(fxp2, make_float2(zcr[r * ZW + 1], zcr[(r + 1) * ZW + 1]), nb2[j]);
 #pragma unroll
               for (int k = 0; k < NR; ++k)
-                nb[j] = fmaf(fk[k], znr[(k * QC + r) * NW + nidx[k]], nb[j]);
+                nb2[j] = __ffma2_rn(fk2[k],
+                                    make_float2(znr[(k * QC + r) * NW + nidx[k]],
+                                                znr[(k * QC + r + 1) * NW + nidx[k]]),
+                                    nb2[j]);
             }
-            float zn[8], tt[8];
+            float zz[8], zn[8], tt[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int r = h + j;
-              zn[j] = fmaxf(0.f, fmaf(e1, zz[j], fmaf(c2, nb[j], c3 * va[r])));
-              tt[j] = zz[j] + va[r];
-              w[r] = r < jn ? beta * (2.f * zn[j] - tt[j]) : 0.f;
+            for (int j = 0; j < 4; ++j) {
+              const int r = h + 2 * j;
+              const float2 va2 = make_float2(va[r], va[r + 1]);
+              const float2 y = __ffma2_rn(e1_2, zz2[j], __ffma2_rn(c2_2, nb2[j], __fmul2_rn(c3_2, va2)));
+              const float2 z2 = make_float2(fmaxf(0.f, y.x), fmaxf(0.f, y.y));
+              const float2 t2 = __fadd2_rn(zz2[j], va2);
+              const float2 w2 =
+                  __fmul2_rn(beta2, __ffma2_rn(two2, z2, make_float2(-t2.x, -t2.y)));
+              zz[2 * j] = zz2[j].x;
+              zz[2 * j + 1] = zz2[j].y;
+              zn[2 * j] = z2.x;
+              zn[2 * j + 1] = z2.y;
+              tt[2 * j] = t2.x;
+              tt[2 * j + 1] = t2.y;
+              // compartments past Q read the copies' zero fill (z) and zero rows of V
+              // (V a): their w is exactly 0 without a test
+              w[r] = w2.x;
+              w[r + 1] = w2.y;
             }
             if constexpr (CHECK) {
               // f^{k+1} = t - d^k / beta needs d^k
@@ -683,9 +750,13 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
         for (int j = 0; j < GC; j += 8) {
           float wh[8], wl[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < 8; k += 2) {
             wh[k] = tf32_rna(w[j + k]);
-            wl[k] = tf32_rna(w[j + k] - wh[k]);
+            wh[k + 1] = tf32_rna(w[j + k + 1]);
+            const float2 l2 = __fadd2_rn(make_float2(w[j + k], w[j + k + 1]),
+                                         make_float2(-wh[k], -wh[k + 1]));
+            wl[k] = tf32_rna(l2.x);
+            wl[k + 1] = tf32_rna(l2.y);
           }
           tst8(tmem + lane_base + L::T_W + 64 * p + grp * GC + j, wh);
           tst8(tmem + lane_base + L::T_W + 64 * p + 32 + grp * GC + j, wl);
