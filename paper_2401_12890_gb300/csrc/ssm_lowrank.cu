@@ -108,8 +108,9 @@ __global__ void __launch_bounds__(NT) lowrank_iter_kernel(const __grid_constant_
                                                           const LowrankArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA destinations must be 128-byte aligned: align the dynamic window explicitly
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  // aligned by an offset from the shared array itself (not through an integer), so that
+  // the compiler keeps the shared address space of every pointer derived from it
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;

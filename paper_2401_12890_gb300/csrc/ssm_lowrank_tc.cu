@@ -271,8 +271,9 @@ __global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_const
   static_assert(L::valid, "two ring stages");
   static_assert(RQ % 8 == 0, "rank split");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  // aligned by an offset from the shared array itself (not through an integer), so that
+  // the compiler keeps the shared address space of every pointer derived from it
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* vring = smem;
   unsigned char* zring = smem + L::zbase;
   uint64_t* vfull = reinterpret_cast<uint64_t*>(zring + NSZ * L::ZST);

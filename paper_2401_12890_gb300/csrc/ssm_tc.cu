@@ -269,8 +269,9 @@ __global__ void __launch_bounds__(NTHR, 1) tc_gemm_kernel(const __grid_constant_
   constexpr uint32_t IDESC = Tile<BN>::IDESC;
   static_assert(C::valid, "fused epilogue needs two ring stages");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  // aligned by an offset from the shared array itself (not through an integer), so that
+  // the compiler keeps the shared address space of every pointer derived from it
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* estage = smem + NS * STAGE_BYTES;      // the epilogue ring (fused)
   uint64_t* full = reinterpret_cast<uint64_t*>(estage + NBE * C::EST);
   uint64_t* empty = full + NS;
