@@ -39,11 +39,12 @@
 // segment order (fixed, hence deterministic). Warp roles:
 //   warp 0      TMA: per chunk, z with its x halo, the -+nx (-+nx*ny) neighbour rows and
 //               the chunk's V / V^T boxes (hi and lo) into a ring of NS stages
-//   warp 1      MMA: product 1 of chunk g, then product 2 of chunk g-1 (so the tensor
-//               core works ahead of the epilogue); commits release stages and buffers
-//   warps 2-17  epilogue, four per TMEM lane quarter, each a quarter of a chunk's
-//               compartments: tcgen05.ld of V a, the z-step and dual step, z' (and d')
-//               stores, w split into TMEM, and the running sum of product 2 in registers
+//   warp 1      MMA: product 1 of chunk g, then product 2 of chunk g - (NVA - 1) (so the
+//               tensor core works ahead of the epilogue); commits release stages and buffers
+//   warps 2-9   epilogue (2-17 on 3D grids and in residual-test iterations), two (four)
+//               per TMEM lane quarter, each a half (quarter) of a chunk's compartments:
+//               tcgen05.ld of V a, the z-step and dual step, z' (and d') stores, w split
+//               into TMEM, and the running sum of product 2 in registers
 // Waiting warps sleep in mbarrier.try_wait (with a suspend-time hint) instead of polling.
 // TMEM: V a (main, correction) and w (hi, lo) are double-buffered by chunk parity, a is
 // per segment, U (main, correction) is double-buffered for RP = 32 and single for 64.
@@ -63,10 +64,11 @@ namespace {
 constexpr int TV = 128;              // voxels per tile: MMA M, TMEM lanes
 constexpr int QC = 32;               // compartments per chunk
 // epilogue warps: 8 on 1D/2D grids, 16 on 3D grids (whose elements read four neighbour
-// rows: more warps hide their longer latency chains); EPQ per TMEM lane quarter, each
-// taking GC compartments of a chunk
-template <int NR> struct Epi {
-  static constexpr int NEPI = NR == 4 ? 16 : 8;
+// rows: more warps hide their longer latency chains) and in residual-test iterations
+// (which also load d^k per element); EPQ per TMEM lane quarter, each taking GC
+// compartments of a chunk
+template <int NR, bool CHECK> struct Epi {
+  static constexpr int NEPI = (NR == 4 || CHECK) ? 16 : 8;
   static constexpr int EPQ = NEPI / 4;
   static constexpr int GC = 32 / EPQ;
   static constexpr int NT = 32 * (2 + NEPI);
@@ -261,10 +263,11 @@ __device__ __forceinline__ void tld2_cols(uint32_t t0, uint32_t t1, float* v0, f
 }
 
 template <int RP, int NR, bool CHECK, bool WD>
-__global__ void __launch_bounds__(Epi<NR>::NT, 1) lrtc_kernel(const __grid_constant__ LrtcMaps maps,
+__global__ void __launch_bounds__(Epi<NR, CHECK>::NT, 1) lrtc_kernel(const __grid_constant__ LrtcMaps maps,
                                                               const LrtcArgs a) {
   using L = Lay<RP, NR>;
-  constexpr int NEPI = Epi<NR>::NEPI, EPQ = Epi<NR>::EPQ, GC = Epi<NR>::GC, NT = Epi<NR>::NT;
+  using E = Epi<NR, CHECK>;
+  constexpr int NEPI = E::NEPI, EPQ = E::EPQ, GC = E::GC, NT = E::NT;
   constexpr int NSV = L::NSV, NSZ = L::NSZ, NVA = L::NVA, UB = L::UB;
   constexpr int D1 = NVA - 1;         // chunks product 1 runs ahead of product 2
   constexpr int RQ = RP / EPQ;        // ranks per epilogue warp of a lane quarter
@@ -855,13 +858,13 @@ ssm_status launch_rn(const LrtcMaps& maps, const LrtcArgs& args, bool check, boo
     const size_t shm = Lay<RP, NR>::bytes;
     const unsigned gr = (unsigned)grid;
     if (check && write_d)
-      lrtc_kernel<RP, NR, true, true><<<gr, Epi<NR>::NT, shm, s>>>(maps, args);
+      lrtc_kernel<RP, NR, true, true><<<gr, Epi<NR, true>::NT, shm, s>>>(maps, args);
     else if (check)
-      lrtc_kernel<RP, NR, true, false><<<gr, Epi<NR>::NT, shm, s>>>(maps, args);
+      lrtc_kernel<RP, NR, true, false><<<gr, Epi<NR, true>::NT, shm, s>>>(maps, args);
     else if (write_d)
-      lrtc_kernel<RP, NR, false, true><<<gr, Epi<NR>::NT, shm, s>>>(maps, args);
+      lrtc_kernel<RP, NR, false, true><<<gr, Epi<NR, false>::NT, shm, s>>>(maps, args);
     else
-      lrtc_kernel<RP, NR, false, false><<<gr, Epi<NR>::NT, shm, s>>>(maps, args);
+      lrtc_kernel<RP, NR, false, false><<<gr, Epi<NR, false>::NT, shm, s>>>(maps, args);
     SSM_LAUNCHED();
     return SSM_OK;
   }
