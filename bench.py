@@ -164,6 +164,18 @@ def traffic_record(kernel_file, kernel_name, workload=None):
     return rec.get("dram_bytes_per_launch_full")
 
 
+def weak_value(world, N, Q, seconds_per_step):
+    """Whole-job throughput under weak scaling: every rank solves its own problem of N
+    voxels and Q compartments, ITERS_PER_STEP iterations per step, and a step takes as
+    long as the slowest rank's (the max over ranks)."""
+    return world * N * Q * ITERS_PER_STEP / seconds_per_step
+
+
+def rank_seed(base_seed, rank):
+    """Each rank's own synthetic problem: the workload's seed offset by the rank."""
+    return base_seed + 7919 * rank
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -299,7 +311,7 @@ def bench_ours(args):
     dist.barrier()
     ssm.load_library()
     w = synth.WORKLOADS[WORKLOAD]
-    K, M, _ = synth.make_problem(WORKLOAD, seed=w.seed + 7919 * dist.rank)
+    K, M, _ = synth.make_problem(WORKLOAD, seed=rank_seed(w.seed, dist.rank))
     N, Q, P = w.N, w.Q, w.P
     Md = torch.from_numpy(M).cuda()
     F = torch.empty((Q, N), dtype=torch.float32, device="cuda")
@@ -433,7 +445,7 @@ def bench_ours(args):
         plan.profile(False)
         ms_max = dist.max(ms)
         per_step = ms_max / steps
-        value = dist.world * N * Q * ITERS_PER_STEP / (per_step / 1e3)
+        value = weak_value(dist.world, N, Q, per_step / 1e3)
         info = plan.solve(Md, F)[1]
         launch = plan.launch_info()
         rec = results.setdefault(key, {})
@@ -478,7 +490,7 @@ def bench_ours(args):
                 plan.solve_host(Mh, Fh)
                 e2e_times.append(time.perf_counter() - t0)
             e2e_s = dist.max(statistics.median(e2e_times))
-            headline["e2e"] = {"value": dist.world * N * Q * ITERS_PER_STEP / e2e_s,
+            headline["e2e"] = {"value": weak_value(dist.world, N, Q, e2e_s),
                                "unit": METRIC, "h2d_bytes_per_step": int(P * N * 4),
                                "d2h_bytes_per_step": int(Q * N * 4)}
             headline["plan_ms"] = info["plan_ms"]
