@@ -50,7 +50,7 @@ METRIC = "voxel*compartment*iters/s"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="auto",
@@ -88,20 +88,40 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    PERIOD_MS = 100
+
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.tmp = None
+        self.skip = 0
 
     def start(self):
+        """Start sampling and return once the sampler has taken its first sample (its
+        start-up would otherwise fall inside a short timed region); that sample and any
+        other taken before this returns are dropped."""
+        self.skip = 0
         try:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=self.tmp, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            lines = self._lines()
+            if lines:
+                self.skip = len(lines)
+                return
+            time.sleep(0.01)
+
+    def _lines(self):
+        self.tmp.flush()
+        with open(self.tmp.name) as f:
+            return [ln for ln in f.read().splitlines() if ln.strip()]
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
@@ -112,9 +132,11 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        self.tmp.flush()
-        rows = [ln.split(",") for ln in open(self.tmp.name).read().splitlines() if ln.strip()]
+        lines = self._lines()
         os.unlink(self.tmp.name)
+        # the samples taken once the timed region had begun; a region shorter than one
+        # period reports the sample taken just before it
+        rows = [ln.split(",") for ln in lines[min(self.skip, max(len(lines) - 1, 0)):]]
         sms, mx, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
