@@ -37,12 +37,13 @@ def fake_tool(tmp_path):
 def test_samples_inside_the_region(tmp_path, monkeypatch):
     import bench
     monkeypatch.setenv("PATH", fake_tool(tmp_path) + os.pathsep + os.environ["PATH"])
+    monkeypatch.setattr(bench.ClockSampler, "PERIOD_MS", 50)
     cs = bench.ClockSampler(0)
     t0 = time.perf_counter()
     cs.start()
     assert time.perf_counter() - t0 >= 0.2          # waited for the tool's first sample
     assert cs.skip >= 1
-    time.sleep(0.4)                                  # the "timed region"
+    time.sleep(0.8)                                  # the "timed region": about 16 periods
     out = cs.stop()
     assert out["samples"] >= 4
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0   # idle sample dropped
