@@ -192,3 +192,25 @@ def test_full_size_sampled_voxels(name, n_iter):
         print(f"{name} {c}: rel err {err:.3e}")
         assert err <= RTOL, (c, err)
     assert F.min() >= 0.0
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "fp32"])
+@pytest.mark.parametrize("name,dims", [("dr2d_tiny", None), ("rr3d_t1t2", (20, 18, 12))])
+def test_residual_tests_leave_the_iterate_unchanged(precision, name, dims):
+    """The iteration kernels with a residual test (which also read d^k, and in the TF32x3
+    form run twice the epilogue warps) and those that store d for the next test must
+    produce the same z as the plain ones: a test at every iteration and a test at none
+    give the same iterate, bit for bit."""
+    w = synth.WORKLOADS[name]
+    dims = dims or w.dims
+    K, M, _ = synth.make_problem(name, dims=dims)
+    Md = torch.from_numpy(np.ascontiguousarray(M)).cuda()
+    out = []
+    for ce, tol in ((0, 0.0), (1, 1e-30), (3, 1e-30)):
+        plan = ssm.Plan(K, dims, w.lam, w.beta, form="lowrank", precision=precision,
+                        max_iter=24, check_every=ce, tol_primal=tol)
+        F, info = plan.solve(Md)
+        assert info["iterations"] == 24
+        out.append(F.clone())
+        plan.close()
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
